@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""K-GRAPE hot-path benchmark: fidelity+gradient evaluations per second on GB300.
+
+One step = one full evaluation (forward Krylov sweep over N slices, target overlap,
+backward co-state sweep with the per-slice overlaps, gradient assembly) of the
+L=20, N=400, m=20 XXZ workload, inputs resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (complex128 NumPy, one thread) on a bounded sample
+of the same workload (one slice forward + one slice backward per step, extrapolated to
+the N-slice evaluation).  Under torchrun each rank runs an independent replica
+(the evaluation does not shard); value = evaluations of all ranks / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+METRIC = "K-GRAPE fidelity+gradient evals/s (L=20,N=400) and HBM % of peak vs FP64"
+UNIT = "evals/s"
+DEFAULT_WORKLOAD = "xxz_L20_N400_m20"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 (complex128) path")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--ctas", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload(name):
+    sys.path.insert(0, ROOT)
+    from paper_2010_03598_gb300 import workloads as W
+    return W, W.WORKLOADS[name]
+
+
+def alg_bytes(w, prec: str, ckpt: int = 0) -> int:
+    """Algorithmic HBM bytes of one evaluation: D-vector passes of the basis-storing Lanczos.
+
+    Per slice and direction: Lanczos step k reads v_k and v_{k-1} (k >= 1) and writes
+    v_{k+1} (k <= m-2): 3m-2 passes; the recombination reads m vectors and writes 1: m+1.
+    The backward sweep reads psi_j once more for the gradient overlap; the target overlap
+    reads 2 vectors.  P = N (2 (4m-1) + 1) + 2, plus N (4m-1) when checkpoints are
+    recomputed.
+    """
+    s = 16 if prec == "c128" else 8
+    P = w.N * (2 * (4 * w.m - 1) + 1) + 2
+    if ckpt:
+        P += w.N * (4 * w.m - 1)
+    return P * w.D * s
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2010_03598_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        ent = d.get(kernel_key)
+        if ent and ent.get("source_hash") == kernel_source_hash():
+            return float(ent["dram_bytes_per_launch_full"])
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd.insert(1, f"--id={self.gpu_id}")
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle
+from paper_2010_03598_gb300 import workloads as W
+w = W.WORKLOADS[{name!r}]
+u, psi0, f = W.instance(w, N={slices})
+ch = oracle.Chain(w.L, w.Jxy, w.Jz)
+t0 = time.perf_counter()
+oracle.segment_forward_backward(ch, u, w.dt, w.m, psi0, f)
+dt = time.perf_counter() - t0
+print(json.dumps(dict(seconds=dt, slices={slices})))
+"""
+
+THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def cpu_baseline(wname: str, w, slices: int = 1):
+    env = dict(os.environ, **THREAD_ENV)
+    code = ORACLE_SNIPPET.format(root=ROOT, name=wname, slices=slices)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    per_eval = d["seconds"] * w.N / slices
+    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{slices} slice(s) forward + backward of the {wname} workload "
+                      f"({d['seconds']:.2f} s), extrapolated x{w.N // slices} to one evaluation; "
+                      "NumPy complex128, 1 thread (OMP/OpenBLAS/MKL = 1)"}
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    for k, v in THREAD_ENV.items():
+        os.environ[k] = v
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    W, w = workload(args.workload)
+    import oracle
+    u, psi0, f = W.instance(w, N=1)
+    ch = oracle.Chain(w.L, w.Jxy, w.Jz)
+    for _ in range(args.warmup):
+        oracle.segment_forward_backward(ch, u, w.dt, w.m, psi0, f)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.segment_forward_backward(ch, u, w.dt, w.m, psi0, f)
+        times.append(time.perf_counter() - t0)
+    per_eval = statistics.mean(times) * w.N
+    value = 1.0 / per_eval
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": config_block(w, args.workload, "c128"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step = 1 slice forward + 1 slice backward of {args.workload} "
+                                   f"(mean {statistics.mean(times):.2f} s), extrapolated x{w.N}; NumPy complex128, "
+                                   "1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def config_block(w, name, prec):
+    return {"workload": name, "L": w.L, "D": w.D, "N": w.N, "m": w.m, "dt": w.dt, "delta": w.delta, "J": w.J,
+            "hc": "Sx on site 1", "psi0": "Neel", "target": "seeded Gaussian, normalised", "prec": prec,
+            "l2": "flushed between timed steps (512 MiB write); per-step working set > L2",
+            "parallelism": "replicas (one independent evaluation per GPU)"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    sys.path.insert(0, ROOT)
+    from paper_2010_03598_gb300 import api as A
+    W, w = workload(args.workload)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    u, psi0, f = W.instance(w)
+    ut = torch.tensor(u, device=dev)
+    pt = torch.tensor(psi0, device=dev)
+    ft = torch.tensor(f, device=dev)
+    chain = A.ChainSpec(w.L, w.Jxy, w.Jz)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(prec, steps, warmup):
+        eng = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec=prec, tile_bits=args.tile_bits, ctas=args.ctas),
+                       device=dev)
+        for _ in range(warmup):
+            eng.evaluate(ut, pt, ft)
+        rep = eng.sync()
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t_wall = time.perf_counter()
+        for e0, e1 in ev:
+            flush.fill_(1)                     # evict L2 between steps (outside the events)
+            e0.record(stream)
+            eng.evaluate(ut, pt, ft)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+        barrier()
+        rep = eng.sync()
+        ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        fid = float(eng.fid.item())
+        eng.close()
+        return ms, rep, fid, t_wall
+
+    gpu_id = None
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        gpu_id = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    except Exception:
+        gpu_id = None
+
+    # --- headline path (timed region sampled for clocks)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    ms, rep, fid, wall = timed(args.prec, args.steps, args.warmup)
+    clocks = sampler.stop()
+    total_s = max_over_ranks(sum(ms) / 1e3)
+    value = args.steps * world / total_s
+    ms_per_step = total_s * 1e3 / args.steps
+    hbm, peak_kind = measured_peaks()
+    per_launch_s = statistics.mean(ms) / 1e3
+    ab = alg_bytes(w, args.prec)
+    achieved = ab / per_launch_s / 1e9
+    kernel_key = f"kg_eval_kernel<{'float2' if args.prec == 'c64' else 'double2'}>@{args.workload}"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": ncu_traffic(kernel_key), "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": ab, "kernel": kernel_key.split("@")[0],
+                "launch_ms": statistics.mean(ms)}
+
+    # --- plain FP64 path, same workload
+    fp64 = None
+    if args.fp64_steps > 0 and args.prec != "c128":
+        ms64, rep64, fid64, _ = timed("c128", args.fp64_steps, 1)
+        t64 = max_over_ranks(sum(ms64) / 1e3)
+        a64 = alg_bytes(w, "c128") / (statistics.mean(ms64) / 1e3) / 1e9
+        fp64 = {"value": args.fp64_steps * world / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.fp64_steps,
+                "steps": args.fp64_steps, "hbm_gbs_algorithmic": a64, "hbm_frac": a64 / hbm,
+                "speedup_of_headline": value / (args.fp64_steps * world / t64),
+                "rel_diff_F_vs_headline": abs(fid - fid64) / abs(fid64)}
+
+    # --- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    eng = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec=args.prec, host_staging=True, tile_bits=args.tile_bits,
+                                    ctas=args.ctas), device=dev)
+    uh = torch.tensor(u).pin_memory()
+    ph = torch.tensor(psi0).pin_memory()
+    fh = torch.tensor(f).pin_memory()
+    fid_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+    grad_h = torch.zeros(w.N, dtype=torch.float64).pin_memory()
+    eng.evaluate_host(uh, ph, fh, fid_h, grad_h)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        eng.evaluate_host(uh, ph, fh, fid_h, grad_h)
+    te = max_over_ranks(time.perf_counter() - t0)
+    eng.close()
+    e2e = {"value": args.e2e_steps * world / te, "unit": UNIT,
+           "h2d_bytes_per_step": int(uh.numel() * 8 + ph.numel() * 16 + fh.numel() * 16),
+           "d2h_bytes_per_step": int(8 + grad_h.numel() * 8), "api": "kg_evaluate_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, w)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64" if args.prec == "c64" else "c128", "data": "synthetic",
+            "config": config_block(w, args.workload, args.prec), "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps, "fp64_path": fp64,
+            "report": {k: rep[k] for k in ("krylov_err_max", "norm_final", "breakdowns", "ctas", "tile_bits",
+                                           "threads")},
+            "F": fid, "wall_s_timed": wall,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

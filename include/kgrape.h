@@ -1,0 +1,178 @@
+/*
+ * kgrape.h - C ABI of the GB300 K-GRAPE hot path (fidelity and gradient of a
+ * piecewise-constant control pulse on an open XXZ chain).
+ *
+ * What is computed (Larocca & Wisniacki, "K-GRAPE", arXiv:2010.03598):
+ *   H_j = H0 + u_{j-1} Hc                       (Eq. htot with the PWC ansatz, Eq. PWC)
+ *   H0  = sum_{b=0}^{L-2} Jxy (Sx_b Sx_{b+1} + Sy_b Sy_{b+1}) + Jz Sz_b Sz_{b+1}   (Eq. H01)
+ *   psi_j = exp(-i dt H_j) psi_{j-1}, j = 1..N, each step by a Lanczos/Krylov
+ *           approximation with an m-vector basis                                   (Appendix A)
+ *   beta = <f|psi_N>, F = |beta|^2 = 1 - I                                         (Eq. objective)
+ *   chi_N = beta f, chi_{j-1} = exp(+i dt H_j) chi_j                                (Alg. "Basic GRAPE", step 6)
+ *   G_j = 2 dt Im <chi_j|Hc|psi_j>, j = 0..N                                        (Eq. gradI)
+ *   dF/du_{j-1} = G_j                (KG_GRAD_ZEROTH: Hc at the end of slice j, Eq. gradI)
+ *   dF/du_{j-1} = (G_{j-1} + G_j)/2  (KG_GRAD_CENTERED: trapezoid over slice j, App. B last paragraph)
+ * Gradients are of the fidelity F (the paper's are of the infidelity I = 1 - F).
+ *
+ * Basis convention: amplitude index i in [0, 2^L); site k (1-based) is bit k-1 of i;
+ * bit value 0 = spin up (Sz = +1/2), as in the spin-up-is-zero encoding of Sec. 3.1.
+ * Complex vectors are interleaved (re, im) pairs: complex128 = two doubles per amplitude.
+ *
+ * Conventions for every entry point:
+ *   - status codes are returned, never thrown; kg_last_error() gives a message for the
+ *     calling thread's last failure;
+ *   - device pointers belong to the caller; the library allocates no device memory:
+ *     every buffer it needs lives in the caller's workspace (size from kg_workspace_bytes);
+ *   - work is enqueued on the caller's CUDA stream and is asynchronous unless stated;
+ *     errors detected on the device (KG_ERR_TIMEOUT, KG_ERR_NONFINITE) are reported by
+ *     kg_sync() after the stream has drained;
+ *   - a handle (and its workspace) serves one evaluation at a time: calls that share a
+ *     handle must be ordered on one stream.
+ */
+#ifndef KGRAPE_H
+#define KGRAPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kg_status {
+  KG_OK = 0,
+  KG_ERR_INVALID_ARG = 1,  /* a pointer, size or option is out of range */
+  KG_ERR_UNSUPPORTED = 2,  /* valid request the library does not implement (e.g. L > 30) */
+  KG_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  KG_ERR_NONFINITE = 4,    /* a Lanczos coefficient or norm became NaN/Inf on the device */
+  KG_ERR_TIMEOUT = 5,      /* a device-side wait (group barrier) ran past its time limit */
+  KG_ERR_WORKSPACE = 6     /* workspace too small or misaligned (256-byte alignment) */
+} kg_status;
+
+typedef enum kg_precision {
+  KG_PREC_C128 = 0,        /* complex128 vectors, FP64 arithmetic throughout */
+  KG_PREC_C64_F64REC = 1   /* complex64 vectors and H*v in FP32; alpha/beta recurrences,
+                              norms, the m x m exponential and <f|psi_N> in FP64 */
+} kg_precision;
+
+typedef enum kg_grad_mode {
+  KG_GRAD_NONE = 0,        /* fidelity only (no backward sweep) */
+  KG_GRAD_CENTERED = 1,    /* (G_{j-1} + G_j) / 2, the gradient fed to L-BFGS in Sec. 2 */
+  KG_GRAD_ZEROTH = 2       /* G_j (Eq. gradI) */
+} kg_grad_mode;
+
+typedef enum kg_hc_kind {
+  KG_HC_SX_SITE = 0,       /* Hc = hc_amp * Sx on site hc_site+1 (bit hc_site) */
+  KG_HC_SZ_SITES = 1       /* Hc = hc_amp * sum over set bits s of hc_site_mask of Sz_s;
+                              Sec. 3.1's (J/2)(sigma^z_1 + sigma^z_L) is hc_amp = J,
+                              mask = 1 | 1 << (L-1) */
+} kg_hc_kind;
+
+/* The chain and its control operator (Eq. H01, Eq. htot). */
+typedef struct kg_chain {
+  int32_t L;               /* number of spins, 1 <= L <= 30; state dimension D = 2^L */
+  int32_t hc_kind;         /* kg_hc_kind */
+  int32_t hc_site;         /* KG_HC_SX_SITE: 0-based site, 0 <= hc_site < L */
+  int32_t reserved0;       /* must be 0 */
+  uint64_t hc_site_mask;   /* KG_HC_SZ_SITES: sites the Sz terms act on (bits < L) */
+  double Jxy;              /* flip-flop coupling: Jxy (SxSx + SySy) per bond */
+  double Jz;               /* Ising coupling: Jz SzSz per bond */
+  double hc_amp;           /* amplitude of Hc */
+} kg_chain;
+
+/* Pulse, Krylov and execution options. */
+typedef struct kg_options {
+  int32_t N;               /* number of PWC slices (controls), N >= 1 */
+  int32_t m;               /* Krylov basis size (vectors), 1 <= m <= 32 */
+  int32_t prec;            /* kg_precision */
+  int32_t grad;            /* kg_grad_mode */
+  int32_t ckpt_every;      /* 0: keep every psi_j for the backward sweep;
+                              C > 0: keep psi_0, psi_C, psi_2C, ... and psi_N, and recompute
+                              each segment forward during the backward sweep */
+  int32_t tile_bits;       /* 0 = automatic; else amplitudes per tile = 2^tile_bits (6..13) */
+  int32_t ctas;            /* 0 = automatic; else CTAs cooperating on the problem */
+  int32_t flags;           /* KG_FLAG_* */
+  double dt;               /* slice length, dt > 0 */
+  double breakdown_tol;    /* <= 0: 1e-12 (C128) or 1e-5 (C64); Lanczos stops when
+                              b_{k+1} <= tol * max(1, max|alpha| + max b) (Alg. "Lanczos",
+                              the b_j > 0 test) */
+} kg_options;
+
+#define KG_FLAG_HOST_STAGING 1u  /* reserve workspace for kg_evaluate_host's input/output copies */
+
+/* Diagnostics of the last evaluation, filled by kg_sync. */
+typedef struct kg_report {
+  double krylov_err_max;   /* max over all slices of ||psi|| b_m |[exp(-i dt T) e_1]_{m-1}| */
+  double norm_final;       /* ||psi_N|| (1 up to rounding and Krylov error) */
+  double beta_re, beta_im; /* <f|psi_N> */
+  int32_t breakdowns;      /* slices whose Lanczos basis ended early (invariant subspace) */
+  int32_t status;          /* device status word (a kg_status) */
+  int32_t launches;        /* kernels launched by the last evaluate call */
+  int32_t ctas;            /* CTAs that cooperated on the problem */
+  int32_t tile_bits;       /* tile size used */
+  int32_t threads;         /* threads per CTA */
+} kg_report;
+
+typedef struct kg_handle kg_handle;   /* opaque host object; owns no device memory */
+
+/* Library version (major*10000 + minor*100 + patch). Never fails. */
+int kg_version(void);
+
+/* Message for the calling thread's most recent failure ("" if none). Never fails. */
+const char* kg_last_error(void);
+
+/* Workspace bytes needed for (chain, opts) on the current device.
+ * Returns KG_ERR_INVALID_ARG / KG_ERR_UNSUPPORTED for bad options. */
+kg_status kg_workspace_bytes(const kg_chain* chain, const kg_options* opts, size_t* bytes);
+
+/* Create a handle bound to the current device, a caller-owned device workspace
+ * (>= kg_workspace_bytes, 256-byte aligned) and a CUDA stream (cudaStream_t; NULL = legacy
+ * default stream).  Chooses the launch configuration.  The workspace must stay valid until
+ * kg_destroy; it holds the Krylov basis, the trajectory psi_0..psi_N (or its checkpoints),
+ * the co-state, barrier counters and reduction slots. */
+kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options* opts,
+                    void* workspace, size_t bytes, void* cuda_stream);
+
+/* One fidelity(+gradient) evaluation, asynchronous on the handle's stream.
+ *   u      [N]        float64, device: controls, u[j-1] acts in slice j
+ *   psi0   [2^L]      complex128, device: initial state
+ *   target [2^L]      complex128, device: target f (the caller normalises it)
+ *   fid    [1]        float64, device: F = |<f|psi_N>|^2
+ *   grad   [N]        float64, device: dF/du (ignored, may be NULL, if opts.grad == NONE)
+ * Inputs are read and outputs written by the device after the call returns; they must stay
+ * valid until the stream reaches this work. */
+kg_status kg_evaluate(kg_handle* handle, const double* u, const void* psi0, const void* target,
+                      double* fid, double* grad);
+
+/* Same evaluation with HOST buffers (same shapes and types as kg_evaluate).  Copies the
+ * inputs into the workspace (the handle must be created with KG_FLAG_HOST_STAGING), runs,
+ * copies F and the gradient back, and waits for the stream.  Pinned host memory makes the
+ * copies asynchronous DMA; pageable memory works but is slower.  Returns device-side errors
+ * directly (it calls kg_sync). */
+kg_status kg_evaluate_host(kg_handle* handle, const double* u, const void* psi0,
+                           const void* target, double* fid, double* grad);
+
+/* Wait for the handle's stream, read the device status word and, if rep != NULL, fill it.
+ * Returns the device status (KG_OK, KG_ERR_TIMEOUT, KG_ERR_NONFINITE) or KG_ERR_CUDA. */
+kg_status kg_sync(kg_handle* handle, kg_report* rep);
+
+/* Destroy the handle (host memory only; the workspace stays the caller's). NULL is a no-op. */
+kg_status kg_destroy(kg_handle* handle);
+
+/* Time limit, in nanoseconds, of every device-side wait of later launches in this process
+ * (default 2e9).  After a wait runs out the kernel sets KG_ERR_TIMEOUT, every CTA leaves at
+ * its next wait, and the launch ends; the context stays usable.  ns must be >= 1. */
+kg_status kg_set_wait_limit_ns(int64_t ns);
+
+/* Test hook for failure detection.  kind 1: in the next launch, CTA 0 does not arrive at
+ * the first group barrier (a member that never joins); the other CTAs' waits, and its own,
+ * run out after the wait limit and the launch ends with KG_ERR_TIMEOUT (read by kg_sync).
+ * Only multi-CTA launches have a group barrier.  The hook applies to one launch and then
+ * clears itself; kind 0 clears it.  Nothing faults, traps or hangs. */
+kg_status kg_debug_set_fault(int32_t kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KGRAPE_H */

@@ -50,13 +50,14 @@ class Chain:
         self._idx = idx
         # Diagonal of H0: Jz/4 per parallel bond, -Jz/4 per antiparallel bond.
         diag = np.zeros(self.D, dtype=np.float64)
-        self._hops = []  # (mask of antiparallel pairs, partner index) per bond
+        self._hops = []  # (rows i with bits b, b+1 antiparallel, their partners i ^ (3 << b)) per bond
         for b in range(self.L - 1):
             bit_b = (idx >> b) & 1
             bit_b1 = (idx >> (b + 1)) & 1
             anti = bit_b != bit_b1
             diag += np.where(anti, -0.25 * self.Jz, 0.25 * self.Jz)
-            self._hops.append((anti, idx ^ (3 << b)))
+            rows = np.nonzero(anti)[0]
+            self._hops.append((rows, rows ^ (3 << b)))
         self._diag0 = diag
         if hc_kind == "sx":
             if not 0 <= self.hc_site < self.L:
@@ -77,8 +78,8 @@ class Chain:
     def apply_H0(self, v: np.ndarray) -> np.ndarray:
         """H0 v for v of shape (D,) or (D, k)."""
         out = self._col(self._diag0, v) * v
-        for anti, partner in self._hops:
-            out = out + 0.5 * self.Jxy * self._col(anti, v) * v[partner]
+        for rows, partner in self._hops:
+            out[rows] += 0.5 * self.Jxy * v[partner]
         return out
 
     def apply_Hc(self, v: np.ndarray) -> np.ndarray:

@@ -52,8 +52,8 @@ def lanczos(apply_H, psi: np.ndarray, m: int, tol: float = DEFAULT_BREAKDOWN_TOL
         x = apply_H(V[k])
         alpha.append(float(np.vdot(V[k], x).real))
         r = x
-        for _ in range(2):  # classical Gram-Schmidt, twice
-            coeff = V[: k + 1].conj() @ r
+        for _ in range(2):  # classical Gram-Schmidt, twice: coeff_i = <v_i|r>
+            coeff = (V[: k + 1] @ r.conj()).conj()
             r = r - coeff @ V[: k + 1]
         b = float(np.linalg.norm(r))
         if k == m - 1:

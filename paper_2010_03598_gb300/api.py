@@ -1,0 +1,185 @@
+"""Python binding of the K-GRAPE C ABI: one evaluation = one call into libkgrape.so.
+
+PyTorch supplies device memory (the workspace and the input/output tensors) and the
+CUDA stream; every step of the computation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import torch
+
+from . import _abi
+from ._abi import check, lib
+
+_PREC = {"c128": _abi.KG_PREC_C128, "c64": _abi.KG_PREC_C64_F64REC}
+_GRAD = {"none": _abi.KG_GRAD_NONE, "centered": _abi.KG_GRAD_CENTERED, "zeroth": _abi.KG_GRAD_ZEROTH}
+
+
+@dataclasses.dataclass(frozen=True)
+class ChainSpec:
+    """Open XXZ chain H0 = sum Jxy (SxSx + SySy) + Jz SzSz with control Hc (Eq. H01, Eq. htot)."""
+
+    L: int
+    Jxy: float = 1.0
+    Jz: float = 0.5
+    hc_kind: str = "sx"      # "sx": hc_amp * Sx on site hc_site+1; "sz": hc_amp * sum_{s in mask} Sz_s
+    hc_site: int = 0
+    hc_mask: int = 0
+    hc_amp: float = 1.0
+
+    def to_c(self) -> _abi.KgChain:
+        kind = {"sx": _abi.KG_HC_SX_SITE, "sz": _abi.KG_HC_SZ_SITES}[self.hc_kind]
+        return _abi.KgChain(self.L, kind, self.hc_site, 0, self.hc_mask, self.Jxy, self.Jz, self.hc_amp)
+
+
+@dataclasses.dataclass(frozen=True)
+class Options:
+    """Pulse (N slices of length dt), Krylov size m and execution options."""
+
+    N: int
+    dt: float
+    m: int
+    prec: str = "c64"         # "c64" (complex64 state, FP64 recurrences) or "c128"
+    grad: str = "centered"    # "none", "centered", "zeroth"
+    ckpt_every: int = 0
+    tile_bits: int = 0
+    ctas: int = 0
+    host_staging: bool = False
+    breakdown_tol: float = 0.0
+
+    def to_c(self) -> _abi.KgOptions:
+        flags = _abi.KG_FLAG_HOST_STAGING if self.host_staging else 0
+        return _abi.KgOptions(self.N, self.m, _PREC[self.prec], _GRAD[self.grad], self.ckpt_every, self.tile_bits,
+                              self.ctas, flags, self.dt, self.breakdown_tol)
+
+
+def workspace_bytes(chain: ChainSpec, opts: Options) -> int:
+    n = ctypes.c_size_t(0)
+    check(lib().kg_workspace_bytes(ctypes.byref(chain.to_c()), ctypes.byref(opts.to_c()), ctypes.byref(n)),
+          "kg_workspace_bytes")
+    return int(n.value)
+
+
+def set_wait_limit_ns(ns: int) -> None:
+    check(lib().kg_set_wait_limit_ns(int(ns)), "kg_set_wait_limit_ns")
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+class KGrape:
+    """One K-GRAPE problem bound to a device workspace and a CUDA stream.
+
+    ``evaluate`` enqueues one fidelity(+gradient) evaluation (asynchronous);
+    ``evaluate_host`` does the same from host buffers and waits; ``sync`` waits and
+    returns the device report.  Calls on one object must not overlap.
+    """
+
+    def __init__(self, chain: ChainSpec, opts: Options, device: int | torch.device | None = None,
+                 stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("KGrape needs a CUDA device; there is no CPU fallback")
+        self.chain, self.opts = chain, opts
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = workspace_bytes(chain, opts)
+        # over-allocate by 256 bytes and align by hand (the ABI wants 256-byte alignment)
+        self._ws_raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws_raw.data_ptr()
+        self._ws_off = (-base) % 256
+        self.workspace_bytes = nbytes
+        h = ctypes.c_void_p(0)
+        with torch.cuda.device(self.device):
+            check(lib().kg_create(ctypes.byref(h), ctypes.byref(chain.to_c()), ctypes.byref(opts.to_c()),
+                                  ctypes.c_void_p(base + self._ws_off), ctypes.c_size_t(nbytes),
+                                  ctypes.c_void_p(self.stream.cuda_stream)), "kg_create")
+        self._h = h
+        self.D = 1 << chain.L
+        self.fid = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.grad = torch.zeros(max(opts.N, 1), dtype=torch.float64, device=self.device)
+
+    def _check_inputs(self, u, psi0, target):
+        N, D = self.opts.N, self.D
+        if u.dtype != torch.float64 or u.numel() != N or not u.is_contiguous():
+            raise ValueError(f"u must be a contiguous float64 tensor of {N} controls")
+        for name, t in (("psi0", psi0), ("target", target)):
+            if t.dtype != torch.complex128 or t.numel() != D or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous complex128 tensor of {D} amplitudes")
+
+    def evaluate(self, u: torch.Tensor, psi0: torch.Tensor, target: torch.Tensor,
+                 fid: torch.Tensor | None = None, grad: torch.Tensor | None = None):
+        """Enqueue F and dF/du on the stream; returns (fid[1], grad[N]) device tensors."""
+        self._check_inputs(u, psi0, target)
+        for name, t in (("u", u), ("psi0", psi0), ("target", target)):
+            if t.device != self.device:
+                raise ValueError(f"{name} must be on {self.device}")
+        fid = self.fid if fid is None else fid
+        grad = self.grad if grad is None else grad
+        with torch.cuda.device(self.device):
+            check(lib().kg_evaluate(self._h, _ptr(u), _ptr(psi0), _ptr(target), _ptr(fid),
+                                    _ptr(grad) if self.opts.grad != "none" else None), "kg_evaluate")
+        return fid, grad[: self.opts.N]
+
+    def evaluate_host(self, u: torch.Tensor, psi0: torch.Tensor, target: torch.Tensor,
+                      fid: torch.Tensor | None = None, grad: torch.Tensor | None = None):
+        """Evaluate from host (CPU, ideally pinned) tensors; waits; returns host (fid, grad)."""
+        if not self.opts.host_staging:
+            raise ValueError("create KGrape with Options(host_staging=True) to use evaluate_host")
+        self._check_inputs(u, psi0, target)
+        for name, t in (("u", u), ("psi0", psi0), ("target", target)):
+            if t.device.type != "cpu":
+                raise ValueError(f"{name} must be a host tensor")
+        if fid is None:
+            fid = torch.zeros(1, dtype=torch.float64)
+        if grad is None:
+            grad = torch.zeros(self.opts.N, dtype=torch.float64)
+        with torch.cuda.device(self.device):
+            check(lib().kg_evaluate_host(self._h, _ptr(u), _ptr(psi0), _ptr(target), _ptr(fid),
+                                         _ptr(grad) if self.opts.grad != "none" else None), "kg_evaluate_host")
+        return fid, grad
+
+    def sync(self) -> dict:
+        """Wait for the stream; raise on a device-side error; return the report."""
+        rep = _abi.KgReport()
+        with torch.cuda.device(self.device):
+            check(lib().kg_sync(self._h, ctypes.byref(rep)), "kg_sync")
+        return {f: getattr(rep, f) for f, _ in rep._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().kg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KGrapeFidelity(torch.autograd.Function):
+    """F(u) with the hand-written adjoint: forward runs the whole forward + co-state
+    sweep in one library call (the backward sweep needs the stored forward states), and
+    backward returns grad_output * dF/du."""
+
+    @staticmethod
+    def forward(ctx, u, engine: KGrape, psi0, target):
+        if engine.opts.grad == "none":
+            raise ValueError("KGrapeFidelity needs an engine created with a gradient mode")
+        fid, grad = engine.evaluate(u.detach(), psi0, target)
+        ctx.save_for_backward(grad.clone())
+        return fid.clone()
+
+    @staticmethod
+    def backward(ctx, g_out):
+        (grad,) = ctx.saved_tensors
+        return g_out * grad, None, None, None
+
+
+def fidelity(u: torch.Tensor, engine: KGrape, psi0: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
+    """Differentiable F(u) (shape [1]) through the K-GRAPE adjoint kernels."""
+    return KGrapeFidelity.apply(u, engine, psi0, target)

@@ -1,0 +1,309 @@
+// Host side of the C ABI declared in include/kgrape.h: argument checks, workspace layout,
+// launch configuration, and the synchronous host-buffer entry point.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "kg_internal.h"
+#include "kg_launch.h"
+#include "kgrape.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<long long> g_wait_limit_ns{2000000000LL};
+std::atomic<int> g_debug_fault{0};
+
+kg_status fail(kg_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+kg_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(KG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+size_t align_up(size_t x) { return (x + kg::kAlign - 1) / kg::kAlign * kg::kAlign; }
+
+struct Layout {
+  size_t ctrl = 0, bar = 0, red = 0, scal = 0, G = 0, nrm = 0;
+  size_t basis = 0, traj = 0, seg = 0, chi = 0;
+  size_t st_u = 0, st_psi0 = 0, st_target = 0, st_fid = 0, st_grad = 0;
+  size_t total = 0;
+  size_t vec_bytes = 0;
+};
+
+kg_status check_args(const kg_chain* ch, const kg_options* o) {
+  if (!ch || !o) return fail(KG_ERR_INVALID_ARG, "chain and options must not be NULL");
+  if (ch->L < 1) return fail(KG_ERR_INVALID_ARG, "L must be >= 1");
+  if (ch->L > kg::kMaxL) return fail(KG_ERR_UNSUPPORTED, "L > 30 is not supported");
+  if (ch->hc_kind != KG_HC_SX_SITE && ch->hc_kind != KG_HC_SZ_SITES)
+    return fail(KG_ERR_INVALID_ARG, "hc_kind must be KG_HC_SX_SITE or KG_HC_SZ_SITES");
+  if (ch->hc_kind == KG_HC_SX_SITE && (ch->hc_site < 0 || ch->hc_site >= ch->L))
+    return fail(KG_ERR_INVALID_ARG, "hc_site must satisfy 0 <= hc_site < L");
+  if (ch->hc_kind == KG_HC_SZ_SITES && (ch->hc_site_mask >> ch->L) != 0)
+    return fail(KG_ERR_INVALID_ARG, "hc_site_mask has bits at or above L");
+  if (ch->reserved0 != 0) return fail(KG_ERR_INVALID_ARG, "reserved0 must be 0");
+  if (!std::isfinite(ch->Jxy) || !std::isfinite(ch->Jz) || !std::isfinite(ch->hc_amp))
+    return fail(KG_ERR_INVALID_ARG, "Jxy, Jz and hc_amp must be finite");
+  if (o->N < 1) return fail(KG_ERR_INVALID_ARG, "N must be >= 1");
+  if (o->m < 1 || o->m > kg::kMaxM) return fail(KG_ERR_INVALID_ARG, "m must satisfy 1 <= m <= 32");
+  if (o->prec != KG_PREC_C128 && o->prec != KG_PREC_C64_F64REC)
+    return fail(KG_ERR_INVALID_ARG, "prec must be KG_PREC_C128 or KG_PREC_C64_F64REC");
+  if (o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED && o->grad != KG_GRAD_ZEROTH)
+    return fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, KG_GRAD_CENTERED or KG_GRAD_ZEROTH");
+  if (o->ckpt_every < 0) return fail(KG_ERR_INVALID_ARG, "ckpt_every must be >= 0");
+  if (o->tile_bits != 0 && (o->tile_bits < 1 || o->tile_bits > 13))
+    return fail(KG_ERR_INVALID_ARG, "tile_bits must be 0 (auto) or 1..13");
+  if (o->ctas < 0 || o->ctas > kg::kMaxCtas) return fail(KG_ERR_INVALID_ARG, "ctas must be 0 (auto) or 1..2048");
+  if ((o->flags & ~KG_FLAG_HOST_STAGING) != 0) return fail(KG_ERR_INVALID_ARG, "unknown flag bits");
+  if (!(o->dt > 0.0) || !std::isfinite(o->dt)) return fail(KG_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (std::isnan(o->breakdown_tol)) return fail(KG_ERR_INVALID_ARG, "breakdown_tol must not be NaN");
+  return KG_OK;
+}
+
+Layout make_layout(const kg_chain* ch, const kg_options* o) {
+  Layout l;
+  const size_t D = (size_t)1 << ch->L;
+  const size_t vb = D * (o->prec == KG_PREC_C128 ? 16 : 8);
+  l.vec_bytes = vb;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  l.ctrl = take(64);   // status words and barrier counter share one memset block
+  l.bar = l.ctrl + 32;
+  l.red = take(sizeof(double) * 2 * kg::kMaxCtas * kg::kNRed);
+  l.scal = take(sizeof(double) * kg::kScCount);
+  l.G = take(sizeof(double) * (size_t)(o->N + 1));
+  l.nrm = take(sizeof(double) * (size_t)(o->N + 1));
+  l.basis = take(vb * (size_t)(o->m > 1 ? o->m - 1 : 1));
+  const int C = o->ckpt_every;
+  size_t ntraj = (C == 0) ? (size_t)o->N + 1 : (size_t)(o->N / C + 1 + (o->N % C != 0 ? 1 : 0));
+  l.traj = take(vb * ntraj);
+  l.seg = take(C == 0 ? 0 : vb * (size_t)(C + 1));
+  l.chi = take(o->grad == KG_GRAD_NONE ? 0 : 2 * vb);
+  if (o->flags & KG_FLAG_HOST_STAGING) {
+    l.st_u = take(sizeof(double) * (size_t)o->N);
+    l.st_psi0 = take(16 * D);
+    l.st_target = take(16 * D);
+    l.st_fid = take(sizeof(double));
+    l.st_grad = take(sizeof(double) * (size_t)o->N);
+  }
+  l.total = off;
+  return l;
+}
+
+int default_tile_bits(const kg_chain* ch, const kg_options* o) {
+  int t = (o->tile_bits > 0) ? o->tile_bits : (o->prec == KG_PREC_C128 ? 11 : 12);
+  if (t > ch->L) t = ch->L;
+  return t;
+}
+
+}  // namespace
+
+struct kg_handle {
+  kg_chain chain;
+  kg_options opts;
+  Layout lay;
+  char* ws = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int ctas = 1;
+  int t_bits = 1;
+  int launches = 0;
+};
+
+extern "C" {
+
+int kg_version(void) { return 100; }
+
+const char* kg_last_error(void) { return g_last_error.c_str(); }
+
+kg_status kg_set_wait_limit_ns(int64_t ns) {
+  if (ns < 1) return fail(KG_ERR_INVALID_ARG, "wait limit must be >= 1 ns");
+  g_wait_limit_ns.store(ns);
+  return KG_OK;
+}
+
+kg_status kg_debug_set_fault(int32_t kind) {
+  if (kind != 0 && kind != 1) return fail(KG_ERR_INVALID_ARG, "fault kind must be 0 or 1");
+  g_debug_fault.store(kind);
+  return KG_OK;
+}
+
+kg_status kg_workspace_bytes(const kg_chain* chain, const kg_options* opts, size_t* bytes) {
+  kg_status st = check_args(chain, opts);
+  if (st != KG_OK) return st;
+  if (!bytes) return fail(KG_ERR_INVALID_ARG, "bytes must not be NULL");
+  *bytes = make_layout(chain, opts).total;
+  return KG_OK;
+}
+
+kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options* opts, void* workspace,
+                    size_t bytes, void* cuda_stream) {
+  if (!handle) return fail(KG_ERR_INVALID_ARG, "handle must not be NULL");
+  *handle = nullptr;
+  kg_status st = check_args(chain, opts);
+  if (st != KG_OK) return st;
+  const Layout lay = make_layout(chain, opts);
+  if (!workspace) return fail(KG_ERR_WORKSPACE, "workspace must not be NULL");
+  if (((uintptr_t)workspace % kg::kAlign) != 0) return fail(KG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (bytes < lay.total)
+    return fail(KG_ERR_WORKSPACE, "workspace too small: need " + std::to_string(lay.total) + " bytes, got " +
+                                      std::to_string(bytes));
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  const int t = default_tile_bits(chain, opts);
+  const int ntiles = 1 << (chain->L - t);
+  int maxc = 0;
+  e = kg::eval_kernel_max_ctas(opts->prec, t, &maxc);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (maxc < 1) return fail(KG_ERR_UNSUPPORTED, "evaluation kernel does not fit on this device");
+  int ctas = (opts->ctas > 0) ? opts->ctas : ntiles;
+  if (ctas > ntiles) ctas = ntiles;
+  if (ctas > maxc) ctas = maxc;
+  if (ctas > kg::kMaxCtas) ctas = kg::kMaxCtas;
+  kg_handle* h = new kg_handle();
+  h->chain = *chain;
+  h->opts = *opts;
+  if (!(h->opts.breakdown_tol > 0.0)) h->opts.breakdown_tol = (opts->prec == KG_PREC_C128) ? 1e-12 : 1e-5;
+  h->lay = lay;
+  h->ws = (char*)workspace;
+  h->bytes = bytes;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->device = dev;
+  h->ctas = ctas;
+  h->t_bits = t;
+  *handle = h;
+  return KG_OK;
+}
+
+static kg_status enqueue(kg_handle* h, const double* u, const void* psi0, const void* target, double* fid,
+                         double* grad) {
+  const kg_chain& ch = h->chain;
+  const kg_options& o = h->opts;
+  kg::EvalParams p{};
+  p.L = ch.L;
+  p.N = o.N;
+  p.m = o.m;
+  p.t_bits = h->t_bits;
+  p.grad_mode = o.grad;
+  p.hc_kind = ch.hc_kind;
+  p.hc_site = ch.hc_site;
+  p.ckpt = o.ckpt_every;
+  p.hc_mask = ch.hc_site_mask;
+  p.Jxy = ch.Jxy;
+  p.Jz = ch.Jz;
+  p.hc_amp = ch.hc_amp;
+  p.dt = o.dt;
+  p.bd_tol = o.breakdown_tol;
+  p.u = u;
+  p.psi0 = (const double*)psi0;
+  p.target = (const double*)target;
+  p.fid = fid;
+  p.grad = grad;
+  char* ws = h->ws;
+  p.basis = ws + h->lay.basis;
+  p.traj = ws + h->lay.traj;
+  p.seg = ws + h->lay.seg;
+  p.chi = ws + h->lay.chi;
+  p.G = (double*)(ws + h->lay.G);
+  p.nrm = (double*)(ws + h->lay.nrm);
+  p.scal = (double*)(ws + h->lay.scal);
+  p.bar = (unsigned long long*)(ws + h->lay.bar);
+  p.red = (double*)(ws + h->lay.red);
+  p.ctrl = (int*)(ws + h->lay.ctrl);
+  p.wait_limit_ns = g_wait_limit_ns.load();
+  p.debug_fault = g_debug_fault.exchange(0);
+  cudaError_t e = cudaMemsetAsync(ws + h->lay.ctrl, 0, 64, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(control block)");
+  e = kg::launch_eval_kernel(o.prec, p, h->ctas, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the evaluation kernel");
+  h->launches = 1;
+  return KG_OK;
+}
+
+kg_status kg_evaluate(kg_handle* h, const double* u, const void* psi0, const void* target, double* fid,
+                      double* grad) {
+  if (!h) return fail(KG_ERR_INVALID_ARG, "handle must not be NULL");
+  if (!u || !psi0 || !target || !fid) return fail(KG_ERR_INVALID_ARG, "u, psi0, target and fid must not be NULL");
+  if (h->opts.grad != KG_GRAD_NONE && !grad) return fail(KG_ERR_INVALID_ARG, "grad must not be NULL");
+  if (((uintptr_t)psi0 % 16) || ((uintptr_t)target % 16) || ((uintptr_t)u % 8) || ((uintptr_t)fid % 8) ||
+      (grad && ((uintptr_t)grad % 8)))
+    return fail(KG_ERR_INVALID_ARG, "psi0/target must be 16-byte aligned, u/fid/grad 8-byte aligned");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return fail(KG_ERR_INVALID_ARG, "current device differs from the handle's device");
+  return enqueue(h, u, psi0, target, fid, grad);
+}
+
+kg_status kg_sync(kg_handle* h, kg_report* rep) {
+  if (!h) return fail(KG_ERR_INVALID_ARG, "handle must not be NULL");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int ctrl[2] = {0, 0};
+  e = cudaMemcpy(ctrl, h->ws + h->lay.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+  if (rep) {
+    double sc[kg::kScCount];
+    e = cudaMemcpy(sc, h->ws + h->lay.scal, sizeof(sc), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(report)");
+    rep->krylov_err_max = sc[kg::kScErrMax];
+    rep->norm_final = sc[kg::kScNormFinal];
+    rep->beta_re = sc[kg::kScBetaRe];
+    rep->beta_im = sc[kg::kScBetaIm];
+    rep->breakdowns = (int32_t)sc[kg::kScBreakdowns];
+    rep->status = ctrl[kg::kCtrlStatus];
+    rep->launches = h->launches;
+    rep->ctas = h->ctas;
+    rep->tile_bits = h->t_bits;
+    rep->threads = kg::kThreads;
+  }
+  const int st = ctrl[kg::kCtrlStatus];
+  if (st == KG_ERR_TIMEOUT) return fail(KG_ERR_TIMEOUT, "a device-side wait ran past its time limit");
+  if (st == KG_ERR_NONFINITE) return fail(KG_ERR_NONFINITE, "non-finite Lanczos coefficient or norm");
+  if (st != 0) return fail(KG_ERR_CUDA, "device status " + std::to_string(st));
+  return KG_OK;
+}
+
+kg_status kg_evaluate_host(kg_handle* h, const double* u, const void* psi0, const void* target, double* fid,
+                           double* grad) {
+  if (!h) return fail(KG_ERR_INVALID_ARG, "handle must not be NULL");
+  if (!(h->opts.flags & KG_FLAG_HOST_STAGING))
+    return fail(KG_ERR_INVALID_ARG, "handle was created without KG_FLAG_HOST_STAGING");
+  if (!u || !psi0 || !target || !fid) return fail(KG_ERR_INVALID_ARG, "u, psi0, target and fid must not be NULL");
+  if (h->opts.grad != KG_GRAD_NONE && !grad) return fail(KG_ERR_INVALID_ARG, "grad must not be NULL");
+  const size_t D = (size_t)1 << h->chain.L;
+  const int N = h->opts.N;
+  char* ws = h->ws;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(ws + h->lay.st_u, u, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(ws + h->lay.st_psi0, psi0, 16 * D, cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(ws + h->lay.st_target, target, 16 * D, cudaMemcpyHostToDevice, h->stream)))
+    return cuda_fail(e, "cudaMemcpyAsync(host inputs)");
+  kg_status st = enqueue(h, (const double*)(ws + h->lay.st_u), ws + h->lay.st_psi0, ws + h->lay.st_target,
+                         (double*)(ws + h->lay.st_fid), (double*)(ws + h->lay.st_grad));
+  if (st != KG_OK) return st;
+  if ((e = cudaMemcpyAsync(fid, ws + h->lay.st_fid, sizeof(double), cudaMemcpyDeviceToHost, h->stream)))
+    return cuda_fail(e, "cudaMemcpyAsync(fid)");
+  if (h->opts.grad != KG_GRAD_NONE &&
+      (e = cudaMemcpyAsync(grad, ws + h->lay.st_grad, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream)))
+    return cuda_fail(e, "cudaMemcpyAsync(grad)");
+  return kg_sync(h, nullptr);
+}
+
+kg_status kg_destroy(kg_handle* h) {
+  delete h;
+  return KG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,212 @@
+// Device helpers: complex vector types, L2-coherent loads/stores, the bounded group
+// barrier with deterministic FP64 reductions, and the small tridiagonal exponential.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kg_internal.h"
+#include "kgrape.h"
+
+namespace kg {
+
+// ---------------------------------------------------------------- vector traits
+template <class V> struct VecTraits;
+template <> struct VecTraits<float2> { using R = float; };
+template <> struct VecTraits<double2> { using R = double; };
+
+template <class V> __device__ __forceinline__ V vmake(typename VecTraits<V>::R a, typename VecTraits<V>::R b);
+template <> __device__ __forceinline__ float2 vmake<float2>(float a, float b) { return make_float2(a, b); }
+template <> __device__ __forceinline__ double2 vmake<double2>(double a, double b) { return make_double2(a, b); }
+
+// Vectors that other CTAs write during a launch are read through L2 only (ld.global.cg):
+// the per-SM L1 is not coherent across CTAs.
+__device__ __forceinline__ float2 ldv(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldv(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ void stv(float2* p, float2 v) { __stcg(p, v); }
+__device__ __forceinline__ void stv(double2* p, double2 v) { __stcg(p, v); }
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------- group context
+// A group is the set of CTAs that cooperate on one problem.  All CTAs of a group are
+// co-resident (cooperative launch), execute the same sequence of barriers/reductions,
+// and therefore agree on every reduced scalar bit for bit.
+struct Group {
+  int rank, size;
+  unsigned long long* bar;   // monotone arrival counter (reset to 0 before each launch)
+  double* red;               // [2][kMaxCtas][kNRed] partial slots, alternating by reduction
+  int* ctrl;                 // status word, abort flag
+  long long wait_limit_ns;
+  int phase;                 // reduction counter (slot parity)
+  int skip_arrival;          // fault injection: do not arrive at the next barrier (then cleared)
+};
+
+struct SmemRed {
+  double warp_part[32 * kNRed];
+  double out[kNRed];
+  int flag;
+};
+
+// Barrier with a time limit.  Returns false (for every thread of the CTA) if the group
+// aborted or this CTA's wait ran past the limit; in the latter case it records
+// KG_ERR_TIMEOUT and raises the abort flag so every other CTA leaves at its next wait.
+__device__ __forceinline__ bool group_barrier(Group& g, SmemRed& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (g.size > 1) {
+      __threadfence();
+      unsigned long long ticket;
+      if (g.skip_arrival) {  // injected fault: this CTA never joins; its own wait runs out too
+        g.skip_arrival = 0;
+        ticket = 0;
+      } else {
+        ticket = atomicAdd(g.bar, 1ull);
+      }
+      const unsigned long long goal = (ticket / (unsigned long long)g.size + 1ull) * (unsigned long long)g.size;
+      unsigned long long t0 = 0;
+      unsigned polls = 0;
+      while (ld_acquire_u64(g.bar) < goal) {
+        if (ld_volatile_i32(g.ctrl + kCtrlAbort)) { ok = 0; break; }
+        if (++polls > 64) {
+          const unsigned long long now = globaltimer_ns();
+          if (t0 == 0) {
+            t0 = now;
+          } else if ((long long)(now - t0) > g.wait_limit_ns) {
+            atomicCAS(g.ctrl + kCtrlStatus, 0, (int)KG_ERR_TIMEOUT);
+            atomicExch(g.ctrl + kCtrlAbort, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    } else if (ld_volatile_i32(g.ctrl + kCtrlAbort)) {
+      ok = 0;
+    }
+    sm.flag = ok;
+  }
+  __syncthreads();
+  return sm.flag != 0;
+}
+
+// Sum NV per-thread values over the whole group.  Order of summation is fixed (warp
+// butterfly, then warps in order, then CTA partials in rank order), so the result is
+// deterministic and identical in every CTA.  Per-thread values may be float (complex64
+// path: partial sums over a handful of amplitudes) or double; everything from the warp
+// level up is float64.
+template <int NV, class A>
+__device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, A (&vals)[NV], double (&out)[NV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm.warp_part[warp * kNRed + v] = (double)vals[v];
+  }
+  __syncthreads();
+  double* slots = g.red + (size_t)(g.phase & 1) * kMaxCtas * kNRed;
+  g.phase++;
+  if (warp < NV) {
+    double s = (lane < nw) ? sm.warp_part[lane * kNRed + warp] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) {
+      if (g.size > 1) __stcg(slots + (size_t)g.rank * kNRed + warp, s);
+      else sm.out[warp] = s;
+    }
+  }
+  if (g.size > 1) {
+    if (!group_barrier(g, sm)) return false;
+    if (warp < NV) {
+      double s = 0.0;
+      for (int r = lane; r < g.size; r += 32) s += __ldcg(slots + (size_t)r * kNRed + warp);
+      s = warp_sum(s);
+      if (lane == 0) sm.out[warp] = s;
+    }
+  } else if (ld_volatile_i32(g.ctrl + kCtrlAbort)) {
+    return false;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = sm.out[v];
+  return true;
+}
+
+// ---------------------------------------------------------------- small exponential
+// c = exp(-i tau T) e_1 for the real symmetric tridiagonal T of order n <= 32
+// (diag alpha[0..n-1], off-diagonal beta[1..n-1]; beta[k] couples k-1 and k),
+// executed by one full warp; lane k holds c_k.  Method: split tau into s equal steps
+// with ||(tau/s) T||_inf <= 1 (Gershgorin row sums) and sum the Taylor series of each
+// step until the remainder bound r^(K+1)/(K+1)! drops below 1e-18.  FP64 throughout.
+__device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const double* beta, int n,
+                                                double tau, double& c_re, double& c_im) {
+  const int lane = threadIdx.x & 31;
+  const bool in = lane < n;
+  const double a = in ? alpha[lane] : 0.0;
+  const double bl = (in && lane >= 1) ? beta[lane] : 0.0;
+  const double bh = (lane + 1 < n) ? beta[lane + 1] : 0.0;
+  const double row = fabs(tau) * (fabs(a) + fabs(bl) + fabs(bh));
+  const double nrm = warp_max(row);
+  int s = (int)ceil(nrm);
+  if (s < 1) s = 1;
+  const double h = tau / (double)s;
+  // number of Taylor terms for radius r = nrm / s <= 1 (FP32 is enough to pick it)
+  const float r = (float)(nrm / (double)s);
+  int K = 0;
+  {
+    float rem = r;  // r^(K+1) / (K+1)!, the first omitted term's bound
+    while (K < 30 && rem >= 1e-18f) { ++K; rem = rem * r / (float)(K + 1); }
+  }
+  double yr = (lane == 0) ? 1.0 : 0.0, yi = 0.0;
+  for (int st = 0; st < s; ++st) {
+    double tr = yr, ti = yi, ar = yr, ai = yi;
+    for (int k = 1; k <= K; ++k) {
+      const double trm = __shfl_up_sync(0xffffffffu, tr, 1), tim = __shfl_up_sync(0xffffffffu, ti, 1);
+      const double trp = __shfl_down_sync(0xffffffffu, tr, 1), tip = __shfl_down_sync(0xffffffffu, ti, 1);
+      const double zr = fma(bl, trm, fma(a, tr, bh * trp));
+      const double zi = fma(bl, tim, fma(a, ti, bh * tip));
+      const double f = h / (double)k;
+      // (-i f) (zr + i zi) = f zi - i f zr
+      tr = in ? f * zi : 0.0;
+      ti = in ? -f * zr : 0.0;
+      ar += tr;
+      ai += ti;
+    }
+    yr = ar;
+    yi = ai;
+  }
+  c_re = yr;
+  c_im = yi;
+}
+
+}  // namespace kg

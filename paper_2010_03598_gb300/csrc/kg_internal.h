@@ -1,0 +1,51 @@
+// Internal structures shared by the host library and the device kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace kg {
+
+constexpr int kMaxM = 32;          // largest Krylov basis (one warp holds T and c)
+constexpr int kMaxL = 30;
+constexpr int kNRed = 4;           // values per reduction slot
+constexpr int kMaxCtas = 2048;     // reduction slots per group
+constexpr size_t kAlign = 256;
+
+// Scalars kept in the workspace (float64 unless stated).
+enum ScalarIdx {
+  kScBetaRe = 0, kScBetaIm = 1, kScErrMax = 2, kScNormFinal = 3, kScBreakdowns = 4,
+  kScCount = 8
+};
+
+// Status words in the control block.
+enum CtrlIdx { kCtrlStatus = 0, kCtrlAbort = 1 };
+
+// Everything one evaluation kernel needs; passed by value as the kernel parameter.
+struct EvalParams {
+  // problem
+  int L, N, m, t_bits;
+  int grad_mode, hc_kind, hc_site, ckpt;
+  unsigned long long hc_mask;
+  double Jxy, Jz, hc_amp, dt, bd_tol;
+  const double* u;          // [N]
+  const double* psi0;       // [2D] complex128 interleaved
+  const double* target;     // [2D] complex128 interleaved
+  double* fid;              // [1]
+  double* grad;             // [N] or null
+  // workspace (vectors are complex64 or complex128 depending on the kernel)
+  void* basis;              // m-1 vectors: Lanczos slots 1..m-1
+  void* traj;               // psi storage: N+1 vectors, or checkpoints (see ckpt layout)
+  void* seg;                // ckpt > 0: C+1 vectors (segment recompute + 2 forward temps)
+  void* chi;                // 2 vectors (co-state ping-pong)
+  double* G;                // [N+1] overlaps
+  double* nrm;              // [N+1] ||psi_j|| of the forward sweep
+  double* scal;             // [kScCount]
+  unsigned long long* bar;  // group barrier counter
+  double* red;              // [2][kMaxCtas][kNRed] reduction slots
+  int* ctrl;                // [kCtrlStatus, kCtrlAbort]
+  long long wait_limit_ns;
+  int debug_fault;          // 1: CTA 0 skips its arrival at the first group barrier
+};
+
+}  // namespace kg

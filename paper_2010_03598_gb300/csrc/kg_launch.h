@@ -1,0 +1,18 @@
+// Launch entry points of the device code, used by the host library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kg_internal.h"
+
+namespace kg {
+
+constexpr int kThreads = 512;  // threads per CTA of the evaluation kernel
+
+// Cooperative launch of the single-problem evaluation kernel (prec = kg_precision).
+cudaError_t launch_eval_kernel(int prec, const EvalParams& p, int ctas, cudaStream_t stream);
+
+// Largest co-resident grid of the evaluation kernel for a tile of 2^t_bits amplitudes.
+cudaError_t eval_kernel_max_ctas(int prec, int t_bits, int* out);
+
+}  // namespace kg

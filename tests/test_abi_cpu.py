@@ -1,0 +1,142 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function that
+include/kgrape.h declares, and rejects bad arguments with the documented status codes."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2010_03598_gb300 import _abi
+from paper_2010_03598_gb300 import build as kbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def header_functions():
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(kg_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(_abi.LIB_PATH):
+        kbuild.build()
+    return _abi.lib()
+
+
+def test_header_declares_functions():
+    names = header_functions()
+    assert "kg_evaluate" in names and "kg_create" in names and len(names) >= 9
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    assert sorted(_abi.SIGNATURES) == header_functions()
+
+
+def test_version_and_error_string(lib):
+    assert lib.kg_version() >= 100
+    assert isinstance(lib.kg_last_error(), bytes)
+
+
+def _chain(**kw):
+    c = dict(L=8, hc_kind=_abi.KG_HC_SX_SITE, hc_site=0, reserved0=0, hc_site_mask=0, Jxy=1.0, Jz=0.5, hc_amp=1.0)
+    c.update(kw)
+    return _abi.KgChain(**c)
+
+
+def _opts(**kw):
+    o = dict(N=64, m=12, prec=_abi.KG_PREC_C128, grad=_abi.KG_GRAD_CENTERED, ckpt_every=0, tile_bits=0, ctas=0,
+             flags=0, dt=0.1, breakdown_tol=0.0)
+    o.update(kw)
+    return _abi.KgOptions(**o)
+
+
+def _ws(lib, chain, opts):
+    n = ctypes.c_size_t(0)
+    st = lib.kg_workspace_bytes(ctypes.byref(chain), ctypes.byref(opts), ctypes.byref(n))
+    return st, n.value
+
+
+def test_workspace_bytes_covers_the_vectors(lib):
+    for prec, s in ((_abi.KG_PREC_C128, 16), (_abi.KG_PREC_C64_F64REC, 8)):
+        for L, N, m, C in ((8, 64, 12, 0), (10, 23, 5, 4), (16, 200, 20, 0), (20, 400, 20, 20)):
+            st, n = _ws(lib, _chain(L=L), _opts(N=N, m=m, prec=prec, ckpt_every=C))
+            assert st == _abi.KG_OK
+            D = 1 << L
+            traj = (N + 1) if C == 0 else (N // C + 1 + (N % C != 0)) + (C + 1)
+            vectors = (m - 1) + traj + 2  # basis slots, trajectory/checkpoints, co-state pair
+            assert n >= vectors * D * s
+            assert n < (vectors + 1) * D * s + (1 << 20)
+    st, n1 = _ws(lib, _chain(L=12), _opts(flags=_abi.KG_FLAG_HOST_STAGING))
+    st, n0 = _ws(lib, _chain(L=12), _opts())
+    assert n1 - n0 >= 2 * 16 * 4096
+
+
+@pytest.mark.parametrize("chain_kw,opts_kw,status", [
+    (dict(L=0), {}, _abi.KG_ERR_INVALID_ARG),
+    (dict(L=31), {}, _abi.KG_ERR_UNSUPPORTED),
+    (dict(hc_site=8), {}, _abi.KG_ERR_INVALID_ARG),
+    (dict(hc_kind=_abi.KG_HC_SZ_SITES, hc_site_mask=1 << 8), {}, _abi.KG_ERR_INVALID_ARG),
+    (dict(hc_kind=7), {}, _abi.KG_ERR_INVALID_ARG),
+    (dict(Jz=float("nan")), {}, _abi.KG_ERR_INVALID_ARG),
+    (dict(reserved0=1), {}, _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(N=0), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(m=0), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(m=33), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(dt=0.0), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(dt=float("inf")), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(prec=5), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(grad=9), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(ckpt_every=-1), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(tile_bits=14), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(ctas=5000), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(flags=8), _abi.KG_ERR_INVALID_ARG),
+])
+def test_invalid_arguments(lib, chain_kw, opts_kw, status):
+    st, _ = _ws(lib, _chain(**chain_kw), _opts(**opts_kw))
+    assert st == status
+    assert len(lib.kg_last_error()) > 0
+
+
+def test_create_rejects_bad_workspace(lib):
+    h = ctypes.c_void_p(0)
+    c, o = _chain(), _opts()
+    assert lib.kg_create(ctypes.byref(h), ctypes.byref(c), ctypes.byref(o), None, 0, None) == _abi.KG_ERR_WORKSPACE
+    assert lib.kg_create(ctypes.byref(h), ctypes.byref(c), ctypes.byref(o), ctypes.c_void_p(256 * 7 + 8), 1 << 30,
+                         None) == _abi.KG_ERR_WORKSPACE
+    assert lib.kg_create(ctypes.byref(h), ctypes.byref(c), ctypes.byref(o), ctypes.c_void_p(256 * 8), 16,
+                         None) == _abi.KG_ERR_WORKSPACE
+    assert h.value is None
+    assert lib.kg_create(None, ctypes.byref(c), ctypes.byref(o), None, 0, None) == _abi.KG_ERR_INVALID_ARG
+
+
+def test_null_handles(lib):
+    assert lib.kg_evaluate(None, None, None, None, None, None) == _abi.KG_ERR_INVALID_ARG
+    assert lib.kg_evaluate_host(None, None, None, None, None, None) == _abi.KG_ERR_INVALID_ARG
+    assert lib.kg_sync(None, None) == _abi.KG_ERR_INVALID_ARG
+    assert lib.kg_destroy(None) == _abi.KG_OK
+
+
+def test_wait_limit_and_fault_hook_arguments(lib):
+    assert lib.kg_set_wait_limit_ns(0) == _abi.KG_ERR_INVALID_ARG
+    assert lib.kg_set_wait_limit_ns(2_000_000_000) == _abi.KG_OK
+    assert lib.kg_debug_set_fault(3) == _abi.KG_ERR_INVALID_ARG
+    assert lib.kg_debug_set_fault(0) == _abi.KG_OK
+
+
+def test_package_import_does_not_need_the_library():
+    import importlib
+
+    import paper_2010_03598_gb300.workloads as w
+    importlib.reload(w)
+    assert w.neel_index(4) == 10

@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA path (through the C ABI) against the complex128 oracle.
+
+Tolerances (relative; gradients normwise, since single components can be ~0):
+  complex128 path:            |dF|/F <= 1e-10, ||dg||/||g|| <= 1e-10
+  complex64 + FP64 recurrences: |dF|/F <= 1e-5,  ||dg||/||g|| <= 1e-4
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2010_03598_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+TOL = {"c128": (1e-10, 1e-10), "c64": (1e-5, 1e-4)}
+
+
+def api():
+    from paper_2010_03598_gb300 import api as A
+    return A
+
+
+def golden(stem):
+    with open(os.path.join(GOLDEN, stem + ".json")) as fh:
+        return json.load(fh)
+
+
+def to_dev(u, psi0, f):
+    dev = torch.device("cuda", 0)
+    return (torch.tensor(u, dtype=torch.float64, device=dev), torch.tensor(psi0, dtype=torch.complex128, device=dev),
+            torch.tensor(f, dtype=torch.complex128, device=dev))
+
+
+def run_gpu(chain, opts, u, psi0, f):
+    A = api()
+    eng = A.KGrape(chain, opts)
+    ut, pt, ft = to_dev(u, psi0, f)
+    fid, grad = eng.evaluate(ut, pt, ft)
+    rep = eng.sync()
+    F = float(fid.item())
+    g = grad.cpu().numpy().copy() if opts.grad != "none" else None
+    eng.close()
+    return F, g, rep
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def nrel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def check(prec, F, g, F_ref, g_ref):
+    tf, tg = TOL[prec]
+    assert rel(F, F_ref) <= tf, (F, F_ref, rel(F, F_ref))
+    if g_ref is not None:
+        assert nrel(g, g_ref) <= tg, nrel(g, g_ref)
+
+
+# ------------------------------------------------------------------ L=8, N=64, m=12
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("mode", ["centered", "zeroth"])
+def test_L8_workload_vs_oracle(prec, mode):
+    w = W.WORKLOADS["xxz_L8_N64_m12"]
+    gd = golden("oracle_xxz_L8_N64_m12")
+    u, psi0, f = W.instance(w)
+    A = api()
+    F, g, rep = run_gpu(A.ChainSpec(w.L, w.Jxy, w.Jz), A.Options(w.N, w.dt, w.m, prec=prec, grad=mode), u, psi0, f)
+    check(prec, F, g, gd[f"F_{mode}"], gd[f"grad_{mode}"])
+    assert rep["status"] == 0
+    assert abs(rep["norm_final"] - 1.0) < (1e-12 if prec == "c128" else 1e-5)
+
+
+# ------------------------------------------------------------------ tiny and ragged shapes
+@pytest.mark.parametrize("L,N,m", [(1, 3, 12), (2, 5, 12), (2, 1, 1), (3, 4, 2), (5, 7, 32), (4, 1, 6)])
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_small_shapes_and_breakdown(L, N, m, prec):
+    rng = np.random.default_rng(1000 + 10 * L + N)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    ch = oracle.Chain(L, 1.0, 0.5)
+    F_ref, g_ref, _ = oracle.evaluate(ch, u, 0.1, m, psi0, f, "centered")
+    A = api()
+    F, g, rep = run_gpu(A.ChainSpec(L, 1.0, 0.5), A.Options(N, 0.1, m, prec=prec), u, psi0, f)
+    check(prec, F, g, F_ref, g_ref)
+
+
+@pytest.mark.parametrize("tile_bits,ctas", [(6, 1), (6, 3), (6, 16), (4, 7), (10, 1), (5, 0)])
+def test_multi_cta_tilings_vs_oracle(tile_bits, ctas):
+    # 2^10 amplitudes cut into 2^tile_bits tiles, dealt round robin to `ctas` CTAs
+    # (ragged when the tile count is not a multiple of the CTA count).
+    L, N, m = 10, 9, 10
+    rng = np.random.default_rng(77)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    ch = oracle.Chain(L, 1.0, 0.7)
+    F_ref, g_ref, _ = oracle.evaluate(ch, u, 0.07, m, psi0, f, "centered")
+    A = api()
+    for prec in ("c128", "c64"):
+        F, g, rep = run_gpu(A.ChainSpec(L, 1.0, 0.7), A.Options(N, 0.07, m, prec=prec, tile_bits=tile_bits,
+                                                                  ctas=ctas), u, psi0, f)
+        check(prec, F, g, F_ref, g_ref)
+
+
+@pytest.mark.parametrize("site", [0, 4, 8])
+def test_sx_control_on_other_sites(site):
+    L, N, m = 9, 6, 12
+    rng = np.random.default_rng(5 + site)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    ch = oracle.Chain(L, 1.0, 0.5, "sx", hc_site=site, hc_amp=0.9)
+    F_ref, g_ref, _ = oracle.evaluate(ch, u, 0.1, m, psi0, f, "zeroth")
+    A = api()
+    F, g, _ = run_gpu(A.ChainSpec(L, 1.0, 0.5, "sx", hc_site=site, hc_amp=0.9),
+                      A.Options(N, 0.1, m, prec="c128", grad="zeroth", tile_bits=5), u, psi0, f)
+    check("c128", F, g, F_ref, g_ref)
+
+
+def test_paper_control_sz_edges():
+    # Sec. 3.1's control Hc = (J/2)(sigma^z_1 + sigma^z_L) = J (Sz_1 + Sz_L)
+    L, N, m = 9, 12, 10
+    mask = 1 | (1 << (L - 1))
+    rng = np.random.default_rng(8)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    ch = oracle.Chain(L, 2.0, 1.0, "sz", hc_mask=mask, hc_amp=1.0)
+    F_ref, g_ref, _ = oracle.evaluate(ch, u, 0.5, m, psi0, f, "centered")
+    A = api()
+    for prec in ("c128", "c64"):
+        F, g, _ = run_gpu(A.ChainSpec(L, 2.0, 1.0, "sz", hc_mask=mask, hc_amp=1.0),
+                          A.Options(N, 0.5, m, prec=prec, tile_bits=6), u, psi0, f)
+        check(prec, F, g, F_ref, g_ref)
+
+
+@pytest.mark.parametrize("C", [1, 4, 7, 23, 40])
+def test_checkpointing_is_bitwise_equal(C):
+    # psi_j recomputed from checkpoints must reproduce the stored trajectory exactly.
+    L, N, m = 10, 23, 8
+    rng = np.random.default_rng(3)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    A = api()
+    for prec in ("c128", "c64"):
+        F0, g0, _ = run_gpu(A.ChainSpec(L), A.Options(N, 0.05, m, prec=prec, tile_bits=6, ctas=5), u, psi0, f)
+        F1, g1, _ = run_gpu(A.ChainSpec(L), A.Options(N, 0.05, m, prec=prec, tile_bits=6, ctas=5, ckpt_every=C),
+                            u, psi0, f)
+        assert F0 == F1
+        assert np.array_equal(g0, g1)
+    ch = oracle.Chain(L, 1.0, 0.5)
+    F_ref, g_ref, _ = oracle.evaluate(ch, u, 0.05, m, psi0, f, "centered")
+    check("c64", F1, g1, F_ref, g_ref)
+
+
+# ------------------------------------------------------------------ L=16, N=200, m=20
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_L16_workload_vs_oracle(prec):
+    w = W.WORKLOADS["xxz_L16_N200_m20"]
+    gd = golden("oracle_xxz_L16_N200_m20")
+    u, psi0, f = W.instance(w)
+    A = api()
+    F, g, rep = run_gpu(A.ChainSpec(w.L, w.Jxy, w.Jz), A.Options(w.N, w.dt, w.m, prec=prec), u, psi0, f)
+    check(prec, F, g, gd["F_centered"], gd["grad_centered"])
+
+
+# ------------------------------------------------------------------ L=20 (the benchmarked chain)
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_L20_short_pulse_vs_oracle(prec):
+    # Full chain size and the benchmark's launch configuration; N=2 keeps the oracle to seconds.
+    w = W.WORKLOADS["xxz_L20_N400_m20"]
+    gd = golden("oracle_xxz_L20_N2_m20")
+    u, psi0, f = W.instance(w, N=2)
+    A = api()
+    for mode in ("centered", "zeroth"):
+        F, g, rep = run_gpu(A.ChainSpec(w.L, w.Jxy, w.Jz), A.Options(2, w.dt, w.m, prec=prec, grad=mode), u, psi0, f)
+        check(prec, F, g, gd[f"F_{mode}"], gd[f"grad_{mode}"])
+
+
+def test_L20_full_pulse_c64_matches_c128_and_is_deterministic():
+    w = W.WORKLOADS["xxz_L20_N400_m20"]
+    u, psi0, f = W.instance(w)
+    A = api()
+    ch = A.ChainSpec(w.L, w.Jxy, w.Jz)
+    F128, g128, rep128 = run_gpu(ch, A.Options(w.N, w.dt, w.m, prec="c128"), u, psi0, f)
+    F64, g64, rep64 = run_gpu(ch, A.Options(w.N, w.dt, w.m, prec="c64"), u, psi0, f)
+    F64b, g64b, _ = run_gpu(ch, A.Options(w.N, w.dt, w.m, prec="c64"), u, psi0, f)
+    assert F64 == F64b and np.array_equal(g64, g64b)
+    check("c64", F64, g64, F128, g128)
+    assert abs(rep128["norm_final"] - 1.0) < 1e-12
+    assert abs(rep64["norm_final"] - 1.0) < 1e-5
+    assert rep128["krylov_err_max"] < 1e-12
+
+
+# ------------------------------------------------------------------ API surface
+def test_autograd_function_returns_the_adjoint_gradient():
+    w = W.WORKLOADS["xxz_L8_N64_m12"]
+    u, psi0, f = W.instance(w)
+    A = api()
+    eng = A.KGrape(A.ChainSpec(w.L, w.Jxy, w.Jz), A.Options(w.N, w.dt, w.m, prec="c128"))
+    ut, pt, ft = to_dev(u, psi0, f)
+    ut.requires_grad_(True)
+    F = A.fidelity(ut, eng, pt, ft)
+    (2.0 * F).sum().backward()
+    gd = golden("oracle_xxz_L8_N64_m12")
+    assert nrel(ut.grad.cpu().numpy() / 2.0, gd["grad_centered"]) <= 1e-10
+    eng.close()
+
+
+def test_host_buffer_entry_point_matches_device_entry_point():
+    w = W.WORKLOADS["xxz_L8_N64_m12"]
+    u, psi0, f = W.instance(w)
+    A = api()
+    eng = A.KGrape(A.ChainSpec(w.L, w.Jxy, w.Jz), A.Options(w.N, w.dt, w.m, prec="c64", host_staging=True))
+    uh = torch.tensor(u).pin_memory()
+    ph = torch.tensor(psi0).pin_memory()
+    fh = torch.tensor(f).pin_memory()
+    Fh, gh = eng.evaluate_host(uh, ph, fh)
+    ut, pt, ft = to_dev(u, psi0, f)
+    Fd, gd_ = eng.evaluate(ut, pt, ft)
+    eng.sync()
+    assert float(Fh.item()) == float(Fd.item())
+    assert np.array_equal(gh.numpy(), gd_.cpu().numpy())
+    eng.close()
+
+
+def test_nonfinite_control_is_reported():
+    A = api()
+    from paper_2010_03598_gb300 import _abi
+    u = np.zeros(4)
+    u[1] = np.nan
+    eng = A.KGrape(A.ChainSpec(8), A.Options(4, 0.1, 8, prec="c128"))
+    ut, pt, ft = to_dev(u, W.neel_state(8), W.draw_target(np.random.default_rng(0), 256))
+    eng.evaluate(ut, pt, ft)
+    with pytest.raises(_abi.KGrapeError) as ei:
+        eng.sync()
+    assert ei.value.status == _abi.KG_ERR_NONFINITE
+    # the context stays usable
+    u[1] = 0.3
+    ut.copy_(torch.tensor(u))
+    eng.evaluate(ut, pt, ft)
+    eng.sync()
+    eng.close()
+
+
+def test_member_that_never_arrives_times_out_cleanly():
+    # Fault injected on the host: CTA 0 skips its first barrier arrival; every wait is
+    # bounded, so the launch ends with KG_ERR_TIMEOUT and the context stays usable.
+    A = api()
+    from paper_2010_03598_gb300 import _abi
+    L = 10
+    eng = A.KGrape(A.ChainSpec(L), A.Options(3, 0.1, 6, prec="c64", tile_bits=6, ctas=4))
+    rng = np.random.default_rng(1)
+    ut, pt, ft = to_dev(rng.uniform(-1, 1, 3), W.neel_state(L), W.draw_target(rng, 1 << L))
+    try:
+        A.set_wait_limit_ns(50_000_000)
+        _abi.check(_abi.lib().kg_debug_set_fault(1), "kg_debug_set_fault")
+        eng.evaluate(ut, pt, ft)
+        with pytest.raises(_abi.KGrapeError) as ei:
+            eng.sync()
+        assert ei.value.status == _abi.KG_ERR_TIMEOUT
+    finally:
+        A.set_wait_limit_ns(2_000_000_000)
+        _abi.lib().kg_debug_set_fault(0)
+    eng.evaluate(ut, pt, ft)
+    assert eng.sync()["status"] == 0
+    eng.close()
