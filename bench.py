@@ -45,13 +45,19 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
+    ap.add_argument("--N", type=int, default=0, help="shorter pulse (profiling a small case); 0 = workload's N")
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, N: int = 0):
     sys.path.insert(0, ROOT)
+    import dataclasses
+
     from paper_2010_03598_gb300 import workloads as W
-    return W, W.WORKLOADS[name]
+    w = W.WORKLOADS[name]
+    if N:
+        w = dataclasses.replace(w, N=N)
+    return W, w
 
 
 def alg_bytes(w, prec: str, ckpt: int = 0) -> int:
@@ -189,7 +195,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    W, w = workload(args.workload)
+    W, w = workload(args.workload, args.N)
     import oracle
     u, psi0, f = W.instance(w, N=1)
     ch = oracle.Chain(w.L, w.Jxy, w.Jz)
@@ -239,7 +245,7 @@ def run_ours(args):
 
     sys.path.insert(0, ROOT)
     from paper_2010_03598_gb300 import api as A
-    W, w = workload(args.workload)
+    W, w = workload(args.workload, args.N)
 
     def barrier():
         if world > 1:
@@ -322,6 +328,20 @@ def run_ours(args):
                 "rel_diff_F_vs_headline": abs(fid - fid64) / abs(fid64)}
 
     # --- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(A, chain, w, args, dev, u, psi0, f, barrier, max_over_ranks, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, w)
+    emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, fp64, rep, fid, wall)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(A, chain, w, args, dev, u, psi0, f, barrier, max_over_ranks, world):
+    import torch
     eng = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec=args.prec, host_staging=True, tile_bits=args.tile_bits,
                                     ctas=args.ctas), device=dev)
     uh = torch.tensor(u).pin_memory()
@@ -337,14 +357,12 @@ def run_ours(args):
         eng.evaluate_host(uh, ph, fh, fid_h, grad_h)
     te = max_over_ranks(time.perf_counter() - t0)
     eng.close()
-    e2e = {"value": args.e2e_steps * world / te, "unit": UNIT,
-           "h2d_bytes_per_step": int(uh.numel() * 8 + ph.numel() * 16 + fh.numel() * 16),
-           "d2h_bytes_per_step": int(8 + grad_h.numel() * 8), "api": "kg_evaluate_host (pinned host buffers)"}
+    return {"value": args.e2e_steps * world / te, "unit": UNIT,
+            "h2d_bytes_per_step": int(uh.numel() * 8 + ph.numel() * 16 + fh.numel() * 16),
+            "d2h_bytes_per_step": int(8 + grad_h.numel() * 8), "api": "kg_evaluate_host (pinned host buffers)"}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload, w)
 
+def emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, fp64, rep, fid, wall):
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -357,8 +375,6 @@ def run_ours(args):
             "F": fid, "wall_s_timed": wall,
         }
         print(json.dumps(out))
-    if world > 1:
-        dist.destroy_process_group()
 
 
 def main():

@@ -31,7 +31,7 @@ size_t align_up(size_t x) { return (x + kg::kAlign - 1) / kg::kAlign * kg::kAlig
 
 struct Layout {
   size_t ctrl = 0, bar = 0, red = 0, scal = 0, G = 0, nrm = 0;
-  size_t basis = 0, traj = 0, seg = 0, chi = 0;
+  size_t basis = 0, traj = 0, seg = 0, chi = 0, wbuf = 0, xbuf = 0;
   size_t st_u = 0, st_psi0 = 0, st_target = 0, st_fid = 0, st_grad = 0;
   size_t total = 0;
   size_t vec_bytes = 0;
@@ -89,6 +89,8 @@ Layout make_layout(const kg_chain* ch, const kg_options* o) {
   l.traj = take(vb * ntraj);
   l.seg = take(C == 0 ? 0 : vb * (size_t)(C + 1));
   l.chi = take(o->grad == KG_GRAD_NONE ? 0 : 2 * vb);
+  l.wbuf = take(2 * vb);
+  l.xbuf = take(vb);
   if (o->flags & KG_FLAG_HOST_STAGING) {
     l.st_u = take(sizeof(double) * (size_t)o->N);
     l.st_psi0 = take(16 * D);
@@ -101,7 +103,9 @@ Layout make_layout(const kg_chain* ch, const kg_options* o) {
 }
 
 int default_tile_bits(const kg_chain* ch, const kg_options* o) {
-  int t = (o->tile_bits > 0) ? o->tile_bits : (o->prec == KG_PREC_C128 ? 11 : 12);
+  const int tmax = kg::max_tile_bits(o->prec);
+  int t = (o->tile_bits > 0) ? o->tile_bits : tmax;
+  if (t > tmax) t = tmax;
   if (t > ch->L) t = ch->L;
   return t;
 }
@@ -118,6 +122,7 @@ struct kg_handle {
   int device = 0;
   int ctas = 1;
   int t_bits = 1;
+  int variant = 0;
   int launches = 0;
 };
 
@@ -164,14 +169,33 @@ kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options*
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   const int t = default_tile_bits(chain, opts);
   const int ntiles = 1 << (chain->L - t);
-  int maxc = 0;
-  e = kg::eval_kernel_max_ctas(opts->prec, t, &maxc);
-  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-  if (maxc < 1) return fail(KG_ERR_UNSUPPORTED, "evaluation kernel does not fit on this device");
-  int ctas = (opts->ctas > 0) ? opts->ctas : ntiles;
-  if (ctas > ntiles) ctas = ntiles;
-  if (ctas > maxc) ctas = maxc;
-  if (ctas > kg::kMaxCtas) ctas = kg::kMaxCtas;
+  // Resident variant when every CTA can keep its tiles in registers/shared memory.
+  int variant = kg::kVariantStreaming;
+  int ctas = 0;
+  const int tpc = kg::resident_tiles_per_cta(opts->prec);
+  if (tpc > 0) {
+    int maxr = 0;
+    e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantResident, t, &maxr);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    int c = (opts->ctas > 0) ? opts->ctas : ntiles;
+    if (c > ntiles) c = ntiles;
+    if (c > maxr) c = maxr;
+    if (c > kg::kMaxCtas) c = kg::kMaxCtas;
+    if (c >= 1 && (long long)c * tpc >= ntiles) {
+      variant = kg::kVariantResident;
+      ctas = c;
+    }
+  }
+  if (variant == kg::kVariantStreaming) {
+    int maxc = 0;
+    e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantStreaming, t, &maxc);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (maxc < 1) return fail(KG_ERR_UNSUPPORTED, "evaluation kernel does not fit on this device");
+    ctas = (opts->ctas > 0) ? opts->ctas : ntiles;
+    if (ctas > ntiles) ctas = ntiles;
+    if (ctas > maxc) ctas = maxc;
+    if (ctas > kg::kMaxCtas) ctas = kg::kMaxCtas;
+  }
   kg_handle* h = new kg_handle();
   h->chain = *chain;
   h->opts = *opts;
@@ -183,6 +207,7 @@ kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options*
   h->device = dev;
   h->ctas = ctas;
   h->t_bits = t;
+  h->variant = variant;
   *handle = h;
   return KG_OK;
 }
@@ -216,6 +241,8 @@ static kg_status enqueue(kg_handle* h, const double* u, const void* psi0, const 
   p.traj = ws + h->lay.traj;
   p.seg = ws + h->lay.seg;
   p.chi = ws + h->lay.chi;
+  p.wbuf = ws + h->lay.wbuf;
+  p.xbuf = ws + h->lay.xbuf;
   p.G = (double*)(ws + h->lay.G);
   p.nrm = (double*)(ws + h->lay.nrm);
   p.scal = (double*)(ws + h->lay.scal);
@@ -226,7 +253,7 @@ static kg_status enqueue(kg_handle* h, const double* u, const void* psi0, const 
   p.debug_fault = g_debug_fault.exchange(0);
   cudaError_t e = cudaMemsetAsync(ws + h->lay.ctrl, 0, 64, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(control block)");
-  e = kg::launch_eval_kernel(o.prec, p, h->ctas, h->stream);
+  e = kg::launch_eval_kernel(o.prec, h->variant, p, h->ctas, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the evaluation kernel");
   h->launches = 1;
   return KG_OK;

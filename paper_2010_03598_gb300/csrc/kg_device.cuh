@@ -31,6 +31,9 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
@@ -68,6 +71,7 @@ struct Group {
   long long wait_limit_ns;
   int phase;                 // reduction counter (slot parity)
   int skip_arrival;          // fault injection: do not arrive at the next barrier (then cleared)
+  unsigned long long epoch;  // barriers passed so far (identical in every CTA of the group)
 };
 
 struct SmemRed {
@@ -79,25 +83,26 @@ struct SmemRed {
 // Barrier with a time limit.  Returns false (for every thread of the CTA) if the group
 // aborted or this CTA's wait ran past the limit; in the latter case it records
 // KG_ERR_TIMEOUT and raises the abort flag so every other CTA leaves at its next wait.
+// Arrival is a release reduction on a monotone counter (no round trip); the k-th barrier
+// of the launch completes when the counter reaches k * size.
 __device__ __forceinline__ bool group_barrier(Group& g, SmemRed& sm) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
     if (g.size > 1) {
       __threadfence();
-      unsigned long long ticket;
       if (g.skip_arrival) {  // injected fault: this CTA never joins; its own wait runs out too
         g.skip_arrival = 0;
-        ticket = 0;
       } else {
-        ticket = atomicAdd(g.bar, 1ull);
+        red_release_add_u64(g.bar, 1ull);
       }
-      const unsigned long long goal = (ticket / (unsigned long long)g.size + 1ull) * (unsigned long long)g.size;
+      g.epoch++;
+      const unsigned long long goal = g.epoch * (unsigned long long)g.size;
       unsigned long long t0 = 0;
       unsigned polls = 0;
       while (ld_acquire_u64(g.bar) < goal) {
         if (ld_volatile_i32(g.ctrl + kCtrlAbort)) { ok = 0; break; }
-        if (++polls > 64) {
+        if (++polls > 256) {
           const unsigned long long now = globaltimer_ns();
           if (t0 == 0) {
             t0 = now;

@@ -1,18 +1,28 @@
 // K-GRAPE evaluation kernel: forward Krylov sweep, target overlap, backward co-state
 // sweep with per-slice gradient overlaps, all in one cooperative persistent launch.
 //
-// Work split.  The 2^L amplitudes are cut into tiles of 2^t contiguous amplitudes; the
-// CTAs of the group own tiles round robin (tile T -> CTA T mod size).  Each Lanczos step
-// of each slice is:
-//   phase A (per own tile): stage v_k's tile in shared memory, form
-//            w = H_j v_k - b_k v_{k-1} with the matrix-free XXZ stencil (bonds inside the
-//            tile from shared memory, bonds that cross into another tile from L2), write w,
-//            accumulate <v_k|w>;                                   -> reduce alpha_k
-//   phase B (per own tile): w <- w - alpha_k v_k, accumulate ||w||^2 -> reduce b_{k+1}
-// (the order of Paige's Lanczos, App. A's Algorithm "Lanczos" with the coefficients
-// taken against the updated vector), with v_{k+1} = w / b_{k+1} kept implicit as a
-// scale.  After m steps every CTA forms c = exp(-i sigma dt T) e_1 (one warp, FP64) and
-// recombines psi' = ||psi|| sum_k c_k v_k for its own tiles (App. A).
+// Work split.  The 2^L amplitudes are cut into tiles of 2^t contiguous amplitudes; CTA r
+// of the group owns tiles r, r + G, r + 2G, ...  A thread owns amplitudes li = tid + j*NT
+// (j < APT) of each of its CTA's tiles, so index bits >= log2(NT) are thread-local.
+//
+// Lanczos step k of a slice (App. A, Algorithm "Lanczos", in Paige's order), one group
+// barrier per step:
+//   v_k      = (W_k - alpha_{k-1} v_{k-1}) / b_k           own amplitudes, stored as basis slot k
+//   H v_k    = diag v_k + (Jxy/2) sum_{bonds inside the tile} v_k[partner]   (shared memory)
+//            + X_k                                                            (bonds leaving the tile)
+//   X_k      = (sum_{bonds leaving the tile} wgt W_k[partner] - alpha_{k-1} X_{k-1}) / b_k
+//   W_{k+1}  = H v_k - b_k v_{k-1}                          stored for the other tiles' partners
+//   alpha_k  = <v_k|W_{k+1}>,  b_{k+1}^2 = ||W_{k+1}||^2 - 2 alpha_k <v_k|W_{k+1}> + alpha_k^2 ||v_k||^2
+// X_k is the part of H v_k that couples to amplitudes of other tiles; the partner set of an
+// amplitude is the same in every step, so X obeys the same two-term recurrence as v and
+// only W's partners are read.  alpha and b come out of one reduction.  After m steps every
+// CTA forms c = exp(-i sigma dt T) e_1 (one warp, FP64) and recombines
+// psi' = ||psi|| sum_k c_k v_k for its own tiles (App. A).
+//
+// Resident variant (RES): every CTA owns at most TPC tiles; W and X of its amplitudes stay in
+// registers and v_k, v_{k-1} of its tiles in shared memory for the whole slice.  Streaming
+// variant: one tile at a time, W from the global W buffer, X from a global scratch vector,
+// v_{k-1} from the basis.
 #include <cuda_runtime.h>
 
 #include "kg_device.cuh"
@@ -22,11 +32,13 @@ namespace kg {
 
 enum ExtraKind { kExtraNone = 0, kExtraOverlapTarget = 1, kExtraGradOverlap = 2 };
 
+constexpr int kLogNT = 9;  // log2(kThreads)
+static_assert((1 << kLogNT) == kThreads, "kLogNT must match kThreads");
+
 struct SmemSlice {
   SmemRed red;
   double alpha[kMaxM];
   double beta[kMaxM + 1];
-  double scale[kMaxM];
   double coef_re[kMaxM];
   double coef_im[kMaxM];
   double err;
@@ -38,167 +50,313 @@ struct Ctx {
   const EvalParams* p;
   Group g;
   SmemSlice* ss;
-  V* s_v;          // one tile of the current Lanczos vector
-  int t, tile, ntiles;
+  V* sv[2];         // shared memory: v_k and v_{k-1} of the own tiles ([TPC][tile] each)
+  V* sx;            // shared memory (resident variant): X of the own tiles ([TPC][tile])
+  int t, tile, ntiles, n_own;
   size_t D;
   unsigned maskL1;  // bonds 0..L-2 in (i ^ i>>1)
   double err_max;
   int breakdowns;
 
   __device__ V* basis_slot(int k) const { return (V*)p->basis + (size_t)(k - 1) * D; }
+  __device__ V* wbuf(int k) const { return (V*)p->wbuf + (size_t)(k & 1) * D; }
+  __device__ size_t tile_base(int c) const { return (size_t)(g.rank + c * g.size) << t; }
 };
 
 template <class V>
-__device__ __forceinline__ V vscale(V a, typename VecTraits<V>::R s) { return vmake<V>(a.x * s, a.y * s); }
+__device__ __forceinline__ V vzero() { return vmake<V>(0, 0); }
 
-// (H0 + u Hc) applied to amplitude gi of v, where v's tile is in shared memory.
-// Partners outside the tile come from `src` (global, scaled by sk).
-template <class V>
-__device__ __forceinline__ V apply_H_amp(const Ctx<V>& c, const V* __restrict__ src,
-                                         typename VecTraits<V>::R sk, unsigned gi, int li,
-                                         typename VecTraits<V>::R hxy, typename VecTraits<V>::R qz,
-                                         typename VecTraits<V>::R cu_sx, typename VecTraits<V>::R cu_sz) {
+// Bonds (and the Sx control) that leave the tile: acc[j] += wgt * src[partner] for the own
+// amplitudes of the tile at `base`.  The partner set depends only on the amplitude index.
+template <class V, int APT>
+__device__ __forceinline__ void add_cross(const Ctx<V>& c, size_t base, const V* __restrict__ src,
+                                          typename VecTraits<V>::R hxy, typename VecTraits<V>::R cu_sx,
+                                          V (&acc)[APT]) {
   using R = typename VecTraits<V>::R;
   const EvalParams& p = *c.p;
-  const V v = c.s_v[li];
-  const unsigned x = (gi ^ (gi >> 1)) & c.maskL1;   // bit b set <=> bits b, b+1 antiparallel
-  const int anti = __popc(x);
-  // diagonal: Jz/4 per parallel bond, -Jz/4 per antiparallel bond
-  R d = qz * (R)((p.L - 1) - 2 * anti);
-  R hr = 0, hi = 0;
+  const int tid = threadIdx.x;
   const int L1 = p.L - 1;
-  const int tin = c.t - 1;  // bonds b < tin stay inside the tile
-  for (int b = 0; b < L1; ++b) {
-    if ((x >> b) & 1u) {
-      V q;
-      if (b < tin) q = c.s_v[li ^ (3 << b)];
-      else q = vscale(ldv(src + (gi ^ (3u << b))), sk);
-      hr += q.x;
-      hi += q.y;
+  const int t = c.t;
+  if (t - 1 >= 0 && t - 1 < L1) {  // bond t-1: bit t-1 inside the tile, bit t outside
+    const int b = t - 1;
+    const unsigned bt = (unsigned)((base >> t) & 1u);
+#pragma unroll
+    for (int j = 0; j < APT; ++j) {
+      const int li = tid + j * kThreads;
+      if (li < c.tile && ((unsigned)(li >> b) & 1u) != bt) {
+        const V q = ldv(src + ((base + li) ^ ((size_t)3 << b)));
+        acc[j].x += hxy * q.x;
+        acc[j].y += hxy * q.y;
+      }
     }
   }
-  R wr = d * v.x + hxy * hr;
-  R wi = d * v.y + hxy * hi;
-  if (p.hc_kind == KG_HC_SX_SITE) {
-    const int s = p.hc_site;
-    V q;
-    if (s < c.t) q = c.s_v[li ^ (1 << s)];
-    else q = vscale(ldv(src + (gi ^ (1u << s))), sk);
-    wr += cu_sx * q.x;
-    wi += cu_sx * q.y;
-  } else {
-    const unsigned mk = (unsigned)p.hc_mask;
-    const R dz = (R)0.5 * (R)(__popc(mk) - 2 * __popc(gi & mk));
-    wr += cu_sz * dz * v.x;
-    wi += cu_sz * dz * v.y;
+  for (int b = t; b < L1; ++b) {  // bits b, b+1 both outside the tile: same for the whole tile
+    if (((base >> b) ^ (base >> (b + 1))) & 1u) {
+      const V* q0 = src + (base ^ ((size_t)3 << b));
+      V q[APT];
+#pragma unroll
+      for (int j = 0; j < APT; ++j) {
+        const int li = tid + j * kThreads;
+        q[j] = (li < c.tile) ? ldv(q0 + li) : vzero<V>();
+      }
+#pragma unroll
+      for (int j = 0; j < APT; ++j) {
+        acc[j].x += hxy * q[j].x;
+        acc[j].y += hxy * q[j].y;
+      }
+    }
   }
-  return vmake<V>(wr, wi);
+  if (p.hc_kind == KG_HC_SX_SITE && p.hc_site >= t) {
+    const V* q0 = src + (base ^ ((size_t)1 << p.hc_site));
+#pragma unroll
+    for (int j = 0; j < APT; ++j) {
+      const int li = tid + j * kThreads;
+      if (li < c.tile) {
+        const V q = ldv(q0 + li);
+        acc[j].x += cu_sx * q.x;
+        acc[j].y += cu_sx * q.y;
+      }
+    }
+  }
+}
+
+// The part of H v that stays inside the tile, for the own amplitudes of one tile whose v is
+// in shared memory `sv`:  hv = diag v + (Jxy/2) sum_{bonds inside the tile} v[partner] + Hc-term.  Bonds are the outer (runtime) loop and the thread's APT amplitudes the inner
+// (unrolled) one, so every bond issues APT independent shared-memory loads.
+template <class V, int APT>
+__device__ __forceinline__ void apply_H_tile(const Ctx<V>& c, size_t base, const V* sv,
+                                             typename VecTraits<V>::R hxy, typename VecTraits<V>::R qz,
+                                             typename VecTraits<V>::R cu_sx, typename VecTraits<V>::R cu_sz,
+                                             V (&hv)[APT]) {
+  using R = typename VecTraits<V>::R;
+  const EvalParams& p = *c.p;
+  const int tid = threadIdx.x;
+  const int tin = c.t - 1;  // bonds b < tin have both bits inside the tile
+  const int T = c.tile;
+#pragma unroll
+  for (int j = 0; j < APT; ++j) hv[j] = vzero<V>();
+  for (int b = 0; b < tin; ++b) {
+#pragma unroll
+    for (int j = 0; j < APT; ++j) {
+      const int li = tid + j * kThreads;
+      if (li < T && (((li >> b) ^ (li >> (b + 1))) & 1)) {
+        const V q = sv[li ^ (3 << b)];
+        hv[j].x += q.x;
+        hv[j].y += q.y;
+      }
+    }
+  }
+  const unsigned mk = (unsigned)p.hc_mask;
+#pragma unroll
+  for (int j = 0; j < APT; ++j) {
+    const int li = tid + j * kThreads;
+    if (li >= T) continue;
+    const unsigned gi = (unsigned)(base + li);
+    const unsigned x = (gi ^ (gi >> 1)) & c.maskL1;  // bit b set <=> bits b, b+1 antiparallel
+    R d = qz * (R)((p.L - 1) - 2 * __popc(x));
+    if (p.hc_kind == KG_HC_SZ_SITES) d += cu_sz * (R)0.5 * (R)(__popc(mk) - 2 * __popc(gi & mk));
+    const V v = sv[li];
+    R wr = d * v.x + hxy * hv[j].x;
+    R wi = d * v.y + hxy * hv[j].y;
+    if (p.hc_kind == KG_HC_SX_SITE && p.hc_site < c.t) {
+      const V q = sv[li ^ (1 << p.hc_site)];
+      wr += cu_sx * q.x;
+      wi += cu_sx * q.y;
+    }
+    hv[j] = vmake<V>(wr, wi);
+  }
 }
 
 // One Krylov step src -> dst (App. A).  tau = sigma * dt.  Returns false on abort.
 // extra == kExtraOverlapTarget: also e = <f|dst> (f = target, complex128).
 // extra == kExtraGradOverlap:   also e.x = Im <dst|Hc|psi_other>.
-template <class V, class A>
-__device__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_src, double uj, double tau, V* dst,
-                             int extra, const V* psi_other, double& nrm_dst, double2& e) {
+template <class V, class A, int APT, int TPC, bool RES>
+__device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_src, double uj, double tau, V* dst, int extra,
+                             const V* psi_other, double& nrm_dst, double2& e) {
   using R = typename VecTraits<V>::R;
   const EvalParams& p = *c.p;
   SmemSlice& ss = *c.ss;
   const int m = p.m;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x;
+  const R hxy = (R)(0.5 * p.Jxy), qz = (R)(0.25 * p.Jz);
+  const R cu_sx = (R)(0.5 * uj * p.hc_amp), cu_sz = (R)(uj * p.hc_amp);
+  const int T = c.tile;
+  constexpr int NB = RES ? TPC : 1;  // tiles held at once
+
+  V W[NB][APT];                    // W_k of the own amplitudes (k = 0: the source vector psi)
+  V X[RES ? 1 : NB][RES ? 1 : APT];  // streaming: part of H v_k leaving the tile (resident: in c.sx)
   int meff = 0;
   bool broke = false;
   double beta_m = 0.0;
-  const R hxy = (R)(0.5 * p.Jxy), qz = (R)(0.25 * p.Jz);
-  const R cu_sx = (R)(0.5 * uj * p.hc_amp), cu_sz = (R)(uj * p.hc_amp);
+  double a_prev = 0.0, b_cur = nrm_src;  // alpha_{k-1}, b_k (b_0 = ||psi||)
+  double amax = 0.0, bmax = 0.0;
 
   if (nrm_src > 0.0) {
-    if (tid == 0) ss.scale[0] = 1.0 / nrm_src;
-    __syncthreads();
-    double amax = 0.0, bmax = 0.0;
     meff = m;
     for (int k = 0; k < m; ++k) {
       const bool last = (k == m - 1);
-      const V* vk = (k == 0) ? src : c.basis_slot(k);
-      const V* vkm1 = (k == 0) ? nullptr : ((k == 1) ? src : c.basis_slot(k - 1));
-      V* w_out = last ? nullptr : c.basis_slot(k + 1);
-      const R sk = (R)ss.scale[k];
-      const R skm1 = (k == 0) ? (R)0 : (R)ss.scale[k - 1];
-      const R bk = (k == 0) ? (R)0 : (R)ss.beta[k];
+      const V* wsrc = (k == 0) ? src : c.wbuf(k);       // W_k (global, all tiles)
+      V* wdst = last ? nullptr : c.wbuf(k + 1);          // W_{k+1}
+      V* vslot = (k == 0) ? nullptr : c.basis_slot(k);  // v_k (normalised)
+      const V* vprev_g = (k == 0) ? nullptr : ((k == 1) ? src : c.basis_slot(k - 1));
+      const R ap = (R)a_prev;
+      const R ib = (R)(1.0 / b_cur);
+      const R bk = (R)b_cur;
+      const R vprev_scale = (k == 1) ? (R)(1.0 / nrm_src) : (R)1;  // slot 0 is psi, unnormalised
+      V* s_cur = c.sv[k & 1];
+      V* s_prev = c.sv[(k & 1) ^ 1];
       A acc[3] = {0, 0, 0};
-      // ---- phase A: w = H v_k - b_k v_{k-1}
-      for (int T = c.g.rank; T < c.ntiles; T += c.g.size) {
-        const size_t base = (size_t)T << c.t;
-        for (int li = tid; li < c.tile; li += nt) c.s_v[li] = vscale(ldv(vk + base + li), sk);
-        __syncthreads();
-        for (int li = tid; li < c.tile; li += nt) {
-          const unsigned gi = (unsigned)(base + li);
-          V w = apply_H_amp<V>(c, vk, sk, gi, li, hxy, qz, cu_sx, cu_sz);
-          if (k > 0) {
-            const V q = ldv(vkm1 + gi);
-            w.x -= bk * (q.x * skm1);
-            w.y -= bk * (q.y * skm1);
+      for (int c0 = 0; c0 < c.n_own; c0 += NB) {
+        // ---- stage 1: v_k of the own amplitudes, partners leaving the tile
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) {
+          const int ct = c0 + cc;
+          if (ct >= c.n_own) break;
+          const size_t base = c.tile_base(ct);
+          V* sc = s_cur + (RES ? cc * T : 0);
+          const V* sp = s_prev + (RES ? cc * T : 0);
+          if (!RES || k == 0) {
+#pragma unroll
+            for (int j = 0; j < APT; ++j) {
+              const int li = tid + j * kThreads;
+              W[cc][j] = (li < T) ? ldv(wsrc + base + li) : vzero<V>();
+            }
           }
-          const V v = c.s_v[li];
-          acc[0] += (A)(v.x * w.x + v.y * w.y);
-          if (last) {
+          V xt[APT];  // X_{k-1}, then X_k
+#pragma unroll
+          for (int j = 0; j < APT; ++j) {
+            const int li = tid + j * kThreads;
+            if (k == 0 || li >= T) xt[j] = vzero<V>();
+            else if (RES) xt[j] = c.sx[cc * T + li];
+            else xt[j] = ldv((const V*)p.xbuf + base + li);
+          }
+#pragma unroll
+          for (int j = 0; j < APT; ++j) {
+            const int li = tid + j * kThreads;
+            if (li >= T) continue;
+            V v;
+            if (k == 0) {
+              v = vmake<V>(W[cc][j].x * ib, W[cc][j].y * ib);
+            } else {
+              V q;
+              if (RES) {
+                q = sp[li];  // normalised v_{k-1}
+              } else {
+                q = ldv(vprev_g + base + li);
+                q.x *= vprev_scale;
+                q.y *= vprev_scale;
+              }
+              v = vmake<V>((W[cc][j].x - ap * q.x) * ib, (W[cc][j].y - ap * q.y) * ib);
+              stv(vslot + base + li, v);
+            }
+            sc[li] = v;
+          }
+          // X_k = (sum wgt W_k[partner] - alpha_{k-1} X_{k-1}) / b_k
+#pragma unroll
+          for (int j = 0; j < APT; ++j) xt[j] = vmake<V>(-ap * xt[j].x, -ap * xt[j].y);
+          add_cross<V, APT>(c, base, wsrc, hxy, cu_sx, xt);
+#pragma unroll
+          for (int j = 0; j < APT; ++j) {
+            const int li = tid + j * kThreads;
+            const V x = vmake<V>(xt[j].x * ib, xt[j].y * ib);
+            if constexpr (RES) {
+              if (li < T) c.sx[cc * T + li] = x;
+            } else {
+              X[0][j] = x;
+            }
+          }
+        }
+        __syncthreads();
+        // ---- stage 2: H v_k, W_{k+1} = H v_k - b_k v_{k-1}, partial sums
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) {
+          const int ct = c0 + cc;
+          if (ct >= c.n_own) break;
+          const size_t base = c.tile_base(ct);
+          const V* sc = s_cur + (RES ? cc * T : 0);
+          const V* sp = s_prev + (RES ? cc * T : 0);
+          apply_H_tile<V, APT>(c, base, sc, hxy, qz, cu_sx, cu_sz, W[cc]);  // W <- (H v_k) inside the tile
+#pragma unroll
+          for (int j = 0; j < APT; ++j) {
+            const int li = tid + j * kThreads;
+            if (li >= T) continue;
+            V w = W[cc][j];
+            V x;
+            if constexpr (RES) x = c.sx[cc * T + li];
+            else x = X[0][j];
+            w.x += x.x;
+            w.y += x.y;
+            if (k > 0) {
+              V q;
+              if (RES) {
+                q = sp[li];
+              } else {
+                q = ldv(vprev_g + base + li);
+                q.x *= vprev_scale;
+                q.y *= vprev_scale;
+              }
+              w.x -= bk * q.x;
+              w.y -= bk * q.y;
+            }
+            const V v = sc[li];
+            acc[0] += (A)(v.x * w.x + v.y * w.y);
             acc[1] += (A)(w.x * w.x + w.y * w.y);
             acc[2] += (A)(v.x * v.x + v.y * v.y);
-          } else {
-            stv(w_out + gi, w);
+            W[cc][j] = w;
+            if (!last) stv(wdst + base + li, w);
+            if constexpr (!RES) stv((V*)p.xbuf + base + li, X[0][j]);
           }
         }
-        __syncthreads();
+        if (!RES) __syncthreads();
       }
-      if (!last) {
-        double out[1];
-        A a1[1] = {acc[0]};
-        if (!group_reduce<1>(c.g, ss.red, a1, out)) return false;
-        const double alpha = out[0];
-        // ---- phase B: w <- w - alpha v_k, ||w||^2
+      double out[3];
+      if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
+      const double alpha = out[0];
+      // ||W - alpha v||^2 = ||W||^2 - 2 alpha <v|W> + alpha^2 ||v||^2, with <v|W> = alpha
+      const double b2 = out[1] - 2.0 * alpha * alpha + alpha * alpha * out[2];
+      double beta = sqrt(fmax(b2, 0.0));
+      if (!isfinite(alpha) || !isfinite(out[1])) {
+        if (tid == 0) { atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_NONFINITE); atomicExch(p.ctrl + kCtrlAbort, 1); }
+        return false;
+      }
+      if (!last && b2 < 1e-3 * out[1]) {
+        // Near an invariant subspace the identity loses the small b_{k+1} to cancellation:
+        // form ||W_{k+1} - alpha_k v_k||^2 explicitly (one more reduction, rare).
         A n1[1] = {0};
         const R ra = (R)alpha;
-        for (int T = c.g.rank; T < c.ntiles; T += c.g.size) {
-          const size_t base = (size_t)T << c.t;
-          for (int li = tid; li < c.tile; li += nt) {
-            const size_t gi = base + li;
-            V w = ldv(w_out + gi);
-            const V v = ldv(vk + gi);
-            w.x -= ra * (v.x * sk);
-            w.y -= ra * (v.y * sk);
-            stv(w_out + gi, w);
-            n1[0] += (A)(w.x * w.x + w.y * w.y);
+        for (int ct = 0; ct < c.n_own; ++ct) {
+          const size_t base = c.tile_base(ct);
+#pragma unroll
+          for (int j = 0; j < APT; ++j) {
+            const int li = tid + j * kThreads;
+            if (li >= T) continue;
+            const V w = ldv(wdst + base + li);
+            V v;
+            if (k == 0) v = vmake<V>(ldv(src + base + li).x * ib, ldv(src + base + li).y * ib);
+            else v = ldv(vslot + base + li);
+            const R rx = w.x - ra * v.x, ry = w.y - ra * v.y;
+            n1[0] += (A)(rx * rx + ry * ry);
           }
         }
-        double out2[1];
-        if (!group_reduce<1>(c.g, ss.red, n1, out2)) return false;
-        const double beta = sqrt(fmax(out2[0], 0.0));
-        if (!isfinite(alpha) || !isfinite(beta)) {
-          if (tid == 0) { atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_NONFINITE); atomicExch(p.ctrl + kCtrlAbort, 1); }
-          return false;
-        }
-        if (tid == 0) ss.alpha[k] = alpha;
-        amax = fmax(amax, fabs(alpha));
-        if (beta <= p.bd_tol * fmax(1.0, amax + bmax)) {
-          meff = k + 1;
-          broke = true;
-          break;
-        }
-        bmax = fmax(bmax, beta);
-        if (tid == 0) { ss.beta[k + 1] = beta; ss.scale[k + 1] = 1.0 / beta; }
-        __syncthreads();
-      } else {
-        double out[3];
-        if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
-        const double alpha = out[0];
-        if (!isfinite(alpha) || !isfinite(out[1])) {
-          if (tid == 0) { atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_NONFINITE); atomicExch(p.ctrl + kCtrlAbort, 1); }
-          return false;
-        }
-        if (tid == 0) ss.alpha[k] = alpha;
-        // ||w - alpha v||^2 = ||w||^2 - 2 alpha <v|w> + alpha^2 ||v||^2, with <v|w> = alpha
-        beta_m = sqrt(fmax(out[1] - 2.0 * alpha * alpha + alpha * alpha * out[2], 0.0));
+        double o1[1];
+        if (!group_reduce<1>(c.g, ss.red, n1, o1)) return false;
+        beta = sqrt(fmax(o1[0], 0.0));
       }
+      if (tid == 0) ss.alpha[k] = alpha;
+      if (last) {
+        beta_m = beta;
+        break;
+      }
+      amax = fmax(amax, fabs(alpha));
+      if (beta <= p.bd_tol * fmax(1.0, amax + bmax)) {
+        meff = k + 1;
+        broke = true;
+        break;
+      }
+      bmax = fmax(bmax, beta);
+      if (tid == 0) ss.beta[k + 1] = beta;
+      a_prev = alpha;
+      b_cur = beta;
     }
   }
   __syncthreads();
@@ -207,32 +365,60 @@ __device__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_src, double uj,
     double cr = 0.0, ci = 0.0;
     if (meff > 0) tridiag_expv_e1(ss.alpha, ss.beta, meff, tau, cr, ci);
     if (tid < meff) {
-      const double f = nrm_src * ss.scale[tid];
+      // basis slot 0 is psi itself (unnormalised); slots k >= 1 hold normalised v_k
+      const double f = (tid == 0) ? 1.0 : nrm_src;
       ss.coef_re[tid] = cr * f;
       ss.coef_im[tid] = ci * f;
     }
-    if (tid == meff - 1 && meff > 0) ss.err = (broke ? 0.0 : nrm_src * beta_m * sqrt(cr * cr + ci * ci));
+    if (tid == meff - 1 && meff > 0) {
+      // a-posteriori indicator nrm * b_m * |c_{m-1}|; where the Taylor series stopped before
+      // reaching index m-1, |c_{m-1}| <= ||tau T||^(m-1) / (m-1)! bounds it instead
+      double cm = sqrt(cr * cr + ci * ci);
+      if (cm == 0.0 && !broke) {
+        double r = 0.0;
+        for (int i = 0; i < meff; ++i)
+          r = fmax(r, fabs(tau) * (fabs(ss.alpha[i]) + (i > 0 ? ss.beta[i] : 0.0) + (i + 1 < meff ? ss.beta[i + 1] : 0.0)));
+        cm = 1.0;
+        for (int i = 1; i < meff; ++i) cm *= r / (double)i;
+      }
+      ss.err = broke ? 0.0 : nrm_src * beta_m * cm;
+    }
   }
   __syncthreads();
-  if (meff > 0) {
-    if (tid == 0) { c.err_max = fmax(c.err_max, ss.err); c.breakdowns += broke ? 1 : 0; }
+  if (meff > 0 && tid == 0) {
+    c.err_max = fmax(c.err_max, ss.err);
+    c.breakdowns += broke ? 1 : 0;
   }
   // ---- recombination dst = sum_k coef_k v_k (+ fused norms / overlaps)
   A nacc[1] = {0};
   double ex[2] = {0.0, 0.0};
-  for (int T = c.g.rank; T < c.ntiles; T += c.g.size) {
-    const size_t base = (size_t)T << c.t;
-    for (int li = tid; li < c.tile; li += nt) {
-      const size_t gi = base + li;
-      R yr = 0, yi = 0;
-      for (int k = 0; k < meff; ++k) {
-        const V q = ldv(((k == 0) ? src : c.basis_slot(k)) + gi);
-        const R a = (R)ss.coef_re[k], b = (R)ss.coef_im[k];
-        yr += a * q.x - b * q.y;
-        yi += a * q.y + b * q.x;
+  for (int ct = 0; ct < c.n_own; ++ct) {
+    const size_t base = c.tile_base(ct);
+    V y[APT];
+#pragma unroll
+    for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
+    for (int k = 0; k < meff; ++k) {
+      const V* s = (k == 0) ? src : c.basis_slot(k);
+      const R a = (R)ss.coef_re[k], b = (R)ss.coef_im[k];
+      V q[APT];
+#pragma unroll
+      for (int j = 0; j < APT; ++j) {
+        const int li = tid + j * kThreads;
+        q[j] = (li < T) ? ldv(s + base + li) : vzero<V>();
       }
-      const V y = vmake<V>(yr, yi);
-      stv(dst + gi, y);
+#pragma unroll
+      for (int j = 0; j < APT; ++j) {
+        y[j].x += a * q[j].x - b * q[j].y;
+        y[j].y += a * q[j].y + b * q[j].x;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < APT; ++j) {
+      const int li = tid + j * kThreads;
+      if (li >= T) continue;
+      const size_t gi = base + li;
+      const R yr = y[j].x, yi = y[j].y;
+      stv(dst + gi, y[j]);
       nacc[0] += (A)(yr * yr + yi * yi);
       if (extra == kExtraOverlapTarget) {
         const double2 f = reinterpret_cast<const double2*>(p.target)[gi];
@@ -251,8 +437,7 @@ __device__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_src, double uj,
           q.x *= dz;
           q.y *= dz;
         }
-        // Im(conj(y) q)
-        ex[0] += (double)(yr * q.y - yi * q.x);
+        ex[0] += (double)(yr * q.y - yi * q.x);  // Im(conj(y) q)
       }
     }
   }
@@ -274,8 +459,8 @@ __device__ bool init_costate(Ctx<V>& c, double2 beta, V* chi, const V* psiN, dou
   using R = typename VecTraits<V>::R;
   const EvalParams& p = *c.p;
   double acc[2] = {0.0, 0.0};
-  for (int T = c.g.rank; T < c.ntiles; T += c.g.size) {
-    const size_t base = (size_t)T << c.t;
+  for (int ct = 0; ct < c.n_own; ++ct) {
+    const size_t base = c.tile_base(ct);
     for (int li = threadIdx.x; li < c.tile; li += blockDim.x) {
       const size_t gi = base + li;
       const double2 f = reinterpret_cast<const double2*>(p.target)[gi];
@@ -311,8 +496,8 @@ __device__ bool init_state(Ctx<V>& c, V* dst, double& nrm) {
   using R = typename VecTraits<V>::R;
   const EvalParams& p = *c.p;
   double acc[1] = {0.0};
-  for (int T = c.g.rank; T < c.ntiles; T += c.g.size) {
-    const size_t base = (size_t)T << c.t;
+  for (int ct = 0; ct < c.n_own; ++ct) {
+    const size_t base = c.tile_base(ct);
     for (int li = threadIdx.x; li < c.tile; li += blockDim.x) {
       const size_t gi = base + li;
       const double2 a = reinterpret_cast<const double2*>(p.psi0)[gi];
@@ -342,7 +527,7 @@ __device__ __forceinline__ V* fwd_slot(const Ctx<V>& c, int j) {
   return (V*)p.seg + (size_t)(C - 1 + (j & 1)) * c.D;
 }
 
-template <class V, class A>
+template <class V, class A, int APT, int TPC, bool RES>
 __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_constant__ EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
@@ -355,13 +540,18 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
   c.g.ctrl = p.ctrl;
   c.g.wait_limit_ns = p.wait_limit_ns;
   c.g.phase = 0;
+  c.g.epoch = 0;
   c.g.skip_arrival = (p.debug_fault == 1 && blockIdx.x == 0) ? 1 : 0;
   c.ss = &ss;
-  c.s_v = reinterpret_cast<V*>(smem_dyn);
   c.t = p.t_bits;
   c.tile = 1 << p.t_bits;
+  constexpr int NB = RES ? TPC : 1;
+  c.sv[0] = reinterpret_cast<V*>(smem_dyn);
+  c.sv[1] = c.sv[0] + (size_t)NB * c.tile;
+  c.sx = c.sv[1] + (size_t)NB * c.tile;
   c.D = (size_t)1 << p.L;
   c.ntiles = (int)(c.D >> p.t_bits);
+  c.n_own = (c.ntiles - c.g.rank + c.g.size - 1) / c.g.size;
   c.maskL1 = (p.L >= 2) ? ((1u << (p.L - 1)) - 1u) : 0u;
   c.err_max = 0.0;
   c.breakdowns = 0;
@@ -373,12 +563,11 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
   if (lead) p.nrm[0] = nrm_prev;
   double2 beta = make_double2(0.0, 0.0);
   for (int j = 1; j <= p.N; ++j) {
-    const double uj = p.u[j - 1];
     double nrm_new;
     double2 e;
     const int extra = (j == p.N) ? kExtraOverlapTarget : kExtraNone;
-    if (!krylov_slice<V, A>(c, fwd_slot<V>(c, j - 1), nrm_prev, uj, p.dt, fwd_slot<V>(c, j), extra, nullptr,
-                            nrm_new, e))
+    if (!krylov_slice<V, A, APT, TPC, RES>(c, fwd_slot<V>(c, j - 1), nrm_prev, p.u[j - 1], p.dt, fwd_slot<V>(c, j),
+                                           extra, nullptr, nrm_new, e))
       return;
     if (lead) p.nrm[j] = nrm_new;
     nrm_prev = nrm_new;
@@ -412,7 +601,8 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
           V* d = (V*)p.seg + (size_t)(i - a - 1) * c.D;
           double nn;
           double2 e;
-          if (!krylov_slice<V, A>(c, prev, np, p.u[i - 1], p.dt, d, kExtraNone, nullptr, nn, e)) return;
+          if (!krylov_slice<V, A, APT, TPC, RES>(c, prev, np, p.u[i - 1], p.dt, d, kExtraNone, nullptr, nn, e))
+            return;
           prev = d;
           np = nn;
         }
@@ -424,8 +614,8 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
         else psi_jm1 = (V*)p.seg + (size_t)(j - 1 - a - 1) * c.D;
         double nn;
         double2 e;
-        if (!krylov_slice<V, A>(c, chi[cur], nchi, p.u[j - 1], -p.dt, chi[cur ^ 1], kExtraGradOverlap, psi_jm1,
-                                nn, e))
+        if (!krylov_slice<V, A, APT, TPC, RES>(c, chi[cur], nchi, p.u[j - 1], -p.dt, chi[cur ^ 1],
+                                               kExtraGradOverlap, psi_jm1, nn, e))
           return;
         if (lead) p.G[j - 1] = 2.0 * p.dt * e.x;
         cur ^= 1;
@@ -450,41 +640,50 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
 }
 
 // ---------------------------------------------------------------- host-side launch helpers
-template <class V, class A>
-static cudaError_t launch_eval(const EvalParams& p, int ctas, cudaStream_t stream) {
-  const size_t smem = ((size_t)1 << p.t_bits) * sizeof(V);
-  auto kern = kg_eval_kernel<V, A>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+struct KernelChoice {
+  const void* fn;
+  size_t smem;
+};
+
+template <class V, class A, int APT, int TPC, bool RES>
+static KernelChoice choice(int t_bits) {
+  constexpr int NB = RES ? TPC : 1;
+  return {(const void*)kg_eval_kernel<V, A, APT, TPC, RES>,
+          (size_t)(RES ? 3 : 2) * NB * ((size_t)1 << t_bits) * sizeof(V)};
+}
+
+// Variants: complex64 resident (<= 2 tiles of <= 4096 amplitudes per CTA), complex64
+// streaming, complex128 streaming (tiles of <= 2048 amplitudes).
+static KernelChoice pick(int prec, int variant, int t_bits) {
+  if (prec == KG_PREC_C128) return choice<double2, double, 4, 1, false>(t_bits);
+  if (variant == kVariantResident) return choice<float2, float, 8, 2, true>(t_bits);
+  return choice<float2, float, 8, 1, false>(t_bits);
+}
+
+int max_tile_bits(int prec) { return prec == KG_PREC_C128 ? kLogNT + 2 : kLogNT + 3; }
+int resident_tiles_per_cta(int prec) { return prec == KG_PREC_C128 ? 0 : 2; }
+
+cudaError_t launch_eval_kernel(int prec, int variant, const EvalParams& p, int ctas, cudaStream_t stream) {
+  KernelChoice k = pick(prec, variant, p.t_bits);
+  cudaError_t err = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
   if (err != cudaSuccess) return err;
   EvalParams pc = p;
   void* args[] = {&pc};
-  return cudaLaunchCooperativeKernel((const void*)kern, dim3(ctas), dim3(kThreads), args, smem, stream);
+  return cudaLaunchCooperativeKernel(k.fn, dim3(ctas), dim3(kThreads), args, k.smem, stream);
 }
 
-template <class V, class A>
-static cudaError_t max_ctas(int t_bits, int* out) {
-  const size_t smem = ((size_t)1 << t_bits) * sizeof(V);
-  auto kern = kg_eval_kernel<V, A>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t eval_kernel_max_ctas(int prec, int variant, int t_bits, int* out) {
+  KernelChoice k = pick(prec, variant, t_bits);
+  cudaError_t err = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, kThreads, k.smem);
   if (err != cudaSuccess) return err;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   *out = per_sm * sms;
   return cudaSuccess;
-}
-
-cudaError_t launch_eval_kernel(int prec, const EvalParams& p, int ctas, cudaStream_t stream) {
-  if (prec == KG_PREC_C128) return launch_eval<double2, double>(p, ctas, stream);
-  return launch_eval<float2, float>(p, ctas, stream);
-}
-
-cudaError_t eval_kernel_max_ctas(int prec, int t_bits, int* out) {
-  if (prec == KG_PREC_C128) return max_ctas<double2, double>(t_bits, out);
-  return max_ctas<float2, float>(t_bits, out);
 }
 
 }  // namespace kg

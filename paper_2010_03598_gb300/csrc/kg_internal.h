@@ -38,6 +38,8 @@ struct EvalParams {
   void* traj;               // psi storage: N+1 vectors, or checkpoints (see ckpt layout)
   void* seg;                // ckpt > 0: C+1 vectors (segment recompute + 2 forward temps)
   void* chi;                // 2 vectors (co-state ping-pong)
+  void* wbuf;               // 2 vectors: W_k of the Lanczos recurrence (ping-pong)
+  void* xbuf;               // 1 vector: tile-leaving part of H v_k (streaming variant)
   double* G;                // [N+1] overlaps
   double* nrm;              // [N+1] ||psi_j|| of the forward sweep
   double* scal;             // [kScCount]

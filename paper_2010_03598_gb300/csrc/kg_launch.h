@@ -9,10 +9,16 @@ namespace kg {
 
 constexpr int kThreads = 512;  // threads per CTA of the evaluation kernel
 
+enum { kVariantStreaming = 0, kVariantResident = 1 };
+
 // Cooperative launch of the single-problem evaluation kernel (prec = kg_precision).
-cudaError_t launch_eval_kernel(int prec, const EvalParams& p, int ctas, cudaStream_t stream);
+cudaError_t launch_eval_kernel(int prec, int variant, const EvalParams& p, int ctas, cudaStream_t stream);
 
 // Largest co-resident grid of the evaluation kernel for a tile of 2^t_bits amplitudes.
-cudaError_t eval_kernel_max_ctas(int prec, int t_bits, int* out);
+cudaError_t eval_kernel_max_ctas(int prec, int variant, int t_bits, int* out);
+
+// Largest tile (log2 amplitudes) of a precision, and tiles a CTA can hold resident (0: none).
+int max_tile_bits(int prec);
+int resident_tiles_per_cta(int prec);
 
 }  // namespace kg

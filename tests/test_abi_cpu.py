@@ -74,7 +74,7 @@ def test_workspace_bytes_covers_the_vectors(lib):
             assert st == _abi.KG_OK
             D = 1 << L
             traj = (N + 1) if C == 0 else (N // C + 1 + (N % C != 0)) + (C + 1)
-            vectors = (m - 1) + traj + 2  # basis slots, trajectory/checkpoints, co-state pair
+            vectors = (m - 1) + traj + 2 + 3  # basis, trajectory/checkpoints, co-state pair, W pair + X
             assert n >= vectors * D * s
             assert n < (vectors + 1) * D * s + (1 << 20)
     st, n1 = _ws(lib, _chain(L=12), _opts(flags=_abi.KG_FLAG_HOST_STAGING))
