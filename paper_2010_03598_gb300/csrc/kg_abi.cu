@@ -182,7 +182,7 @@ kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options*
     if (c > maxr) c = maxr;
     if (c > kg::kMaxCtas) c = kg::kMaxCtas;
     if (c >= 1 && (long long)c * tpc >= ntiles) {
-      variant = kg::kVariantResident;
+      variant = (t == kg::max_tile_bits(opts->prec)) ? kg::kVariantResidentFull : kg::kVariantResident;
       ctas = c;
     }
   }

@@ -167,12 +167,9 @@ __device__ __forceinline__ void apply_H_tile(const Ctx<V>& c, size_t base, const
   }
 }
 
-// One Krylov step src -> dst (App. A).  tau = sigma * dt.  Returns false on abort.
-// extra == kExtraOverlapTarget: also e = <f|dst> (f = target, complex128).
-// extra == kExtraGradOverlap:   also e.x = Im <dst|Hc|psi_other>.
 template <class V, class A, int APT, int TPC, bool RES>
-__device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_src, double uj, double tau, V* dst, int extra,
-                             const V* psi_other, double& nrm_dst, double2& e) {
+__device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double nrm_src, double uj, int& meff_out,
+                                                bool& broke_out, double& beta_m_out) {
   using R = typename VecTraits<V>::R;
   const EvalParams& p = *c.p;
   SmemSlice& ss = *c.ss;
@@ -359,6 +356,25 @@ __device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_sr
       b_cur = beta;
     }
   }
+  meff_out = meff;
+  broke_out = broke;
+  beta_m_out = beta_m;
+  return true;
+}
+
+// Small exponential c = exp(-i tau T) e_1 and recombination dst = ||src|| sum_k c_k v_k of the
+// own tiles (App. A), with fused ||dst||^2 and the optional overlap:
+// extra == kExtraOverlapTarget: e = <f|dst> (f = target, complex128);
+// extra == kExtraGradOverlap:   e.x = Im <dst|Hc|psi_other>.
+template <class V, class A, int APT>
+__device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm_src, double tau, int meff, bool broke,
+                                             double beta_m, V* dst, int extra, const V* psi_other, double& nrm_dst,
+                                             double2& e) {
+  using R = typename VecTraits<V>::R;
+  const EvalParams& p = *c.p;
+  SmemSlice& ss = *c.ss;
+  const int tid = threadIdx.x;
+  const int T = c.tile;
   __syncthreads();
   // ---- small exponential and recombination coefficients (warp 0)
   if (tid < 32) {
@@ -453,6 +469,220 @@ __device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_sr
   return true;
 }
 
+// Packed FP32x2 helpers (Blackwell FADD2/FMUL2/FFMA2) for complex64 arithmetic.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Lanczos loop of one slice for complex64 tiles of 4096 amplitudes (512 threads x 8), every
+// CTA holding its (at most 2) tiles resident.  Same recurrence as lanczos_generic; the
+// amplitude of thread tid in register j is li = tid + 512 j, so
+//   bonds 0..7  (bits inside tid):  antiparallel test shared by all j, partner (tid ^ 3<<b) + 512 j
+//   bond 8      (bit 8 of tid, bit 0 of j): partner (tid ^ 256) + 512 (j ^ 1)
+//   bonds 9, 10 (bits of j):        partner in registers, test known at compile time
+//   bond 11 and up:                 other tiles (X recurrence, stage 1)
+__device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, double nrm_src, double uj,
+                                           int& meff_out, bool& broke_out, double& beta_m_out) {
+  const EvalParams& p = *c.p;
+  SmemSlice& ss = *c.ss;
+  constexpr int APT = 8, NB = 2, T = 4096, NT = kThreads;
+  const int m = p.m;
+  const int tid = threadIdx.x;
+  const float hxy = (float)(0.5 * p.Jxy), qz = (float)(0.25 * p.Jz);
+  const float cu_sx = (float)(0.5 * uj * p.hc_amp), cu_sz = (float)(uj * p.hc_amp);
+  const unsigned mk = (unsigned)p.hc_mask;
+  const bool hc_sx = (p.hc_kind == KG_HC_SX_SITE);
+  const int hs = p.hc_site;
+  const int L1 = p.L - 1;
+  const unsigned xt = (unsigned)(tid ^ (tid >> 1));
+  const int t8 = (tid >> 8) & 1;
+  const int n_own = c.n_own;
+  float2 W[NB][APT];
+  int meff = m;
+  bool broke = false;
+  double beta_m = 0.0;
+  double a_prev = 0.0, b_cur = nrm_src, amax = 0.0, bmax = 0.0;
+  if (!(nrm_src > 0.0)) {
+    meff_out = 0;
+    broke_out = false;
+    beta_m_out = 0.0;
+    return true;
+  }
+  for (int k = 0; k < m; ++k) {
+    const bool last = (k == m - 1);
+    const float2* wsrc = (k == 0) ? src : c.wbuf(k);
+    float2* wdst = last ? nullptr : c.wbuf(k + 1);
+    float2* vslot = (k == 0) ? nullptr : c.basis_slot(k);
+    const float ap = (float)a_prev, ib = (float)(1.0 / b_cur), bk = (float)b_cur;
+    float2* s_cur = c.sv[k & 1];
+    const float2* s_prev = c.sv[(k & 1) ^ 1];
+    float2 acc_a = f2(0.f), acc_n = f2(0.f), acc_q = f2(0.f);
+    // ---- stage 1: v_k of the own amplitudes; X_k from the partners in other tiles
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) {
+      if (cc >= n_own) break;
+      const size_t base = c.tile_base(cc);
+      float2* sc = s_cur + cc * T;
+      const float2* sp = s_prev + cc * T;
+      float2* sx = c.sx + cc * T;
+      if (k == 0) {
+#pragma unroll
+        for (int j = 0; j < APT; ++j) W[cc][j] = ldv(src + base + tid + j * NT);
+      }
+      float2 x[APT];
+#pragma unroll
+      for (int j = 0; j < APT; ++j) {
+        const int li = tid + j * NT;
+        float2 v;
+        if (k == 0) {
+          v = f2mul(W[cc][j], f2(ib));
+          x[j] = f2(0.f);
+        } else {
+          v = f2mul(f2fma(f2(-ap), sp[li], W[cc][j]), f2(ib));
+          stv(vslot + base + li, v);
+          x[j] = f2mul(f2(-ap), sx[li]);
+        }
+        sc[li] = v;
+      }
+      if (L1 > 11) {  // bond 11: bit 11 = bit 2 of j, bit 12 = lowest tile bit
+        const int bt = (int)((base >> 12) & 1u);
+        const float2* q0 = wsrc + (base ^ ((size_t)1 << 12)) + tid;
+#pragma unroll
+        for (int j = 0; j < APT; ++j)
+          if (((j >> 2) & 1) != bt) x[j] = f2fma(f2(hxy), ldv(q0 + (j ^ 4) * NT), x[j]);
+      }
+      for (int b = 12; b < L1; ++b) {  // bonds between tile bits: the same for the whole tile
+        if (((base >> b) ^ (base >> (b + 1))) & 1u) {
+          const float2* q0 = wsrc + (base ^ ((size_t)3 << b)) + tid;
+          float2 q[APT];
+#pragma unroll
+          for (int j = 0; j < APT; ++j) q[j] = ldv(q0 + j * NT);
+#pragma unroll
+          for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(hxy), q[j], x[j]);
+        }
+      }
+      if (hc_sx && hs >= 12) {
+        const float2* q0 = wsrc + (base ^ ((size_t)1 << hs)) + tid;
+#pragma unroll
+        for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(cu_sx), ldv(q0 + j * NT), x[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < APT; ++j) sx[tid + j * NT] = f2mul(x[j], f2(ib));
+    }
+    __syncthreads();
+    // ---- stage 2: W_{k+1} = H v_k - b_k v_{k-1}; partial sums
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) {
+      if (cc >= n_own) break;
+      const size_t base = c.tile_base(cc);
+      const float2* sc = s_cur + cc * T;
+      const float2* sp = s_prev + cc * T;
+      const float2* sx = c.sx + cc * T;
+      float2 h[APT];
+#pragma unroll
+      for (int j = 0; j < APT; ++j) h[j] = f2(0.f);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        if ((xt >> b) & 1u) {
+          const float2* ps = sc + (tid ^ (3 << b));
+#pragma unroll
+          for (int j = 0; j < APT; ++j) h[j] = f2add(h[j], ps[j * NT]);
+        }
+      }
+      {
+        const float2* ps = sc + (tid ^ 256);
+#pragma unroll
+        for (int j = 0; j < APT; ++j)
+          if (t8 != (j & 1)) h[j] = f2add(h[j], ps[(j ^ 1) * NT]);
+      }
+      float2 v[APT];
+#pragma unroll
+      for (int j = 0; j < APT; ++j) v[j] = sc[tid + j * NT];
+#pragma unroll
+      for (int j = 0; j < APT; ++j) {
+        if ((j ^ (j >> 1)) & 1) h[j] = f2add(h[j], v[j ^ 3]);         // bond 9
+        if (((j >> 1) ^ (j >> 2)) & 1) h[j] = f2add(h[j], v[j ^ 6]);  // bond 10
+      }
+#pragma unroll
+      for (int j = 0; j < APT; ++j) {
+        const int li = tid + j * NT;
+        const unsigned gi = (unsigned)(base + li);
+        const unsigned xg = (gi ^ (gi >> 1)) & c.maskL1;
+        float d = qz * (float)(L1 - 2 * __popc(xg));
+        if (!hc_sx) d += cu_sz * 0.5f * (float)(__popc(mk) - 2 * __popc(gi & mk));
+        float2 w = f2fma(f2(d), v[j], f2fma(f2(hxy), h[j], sx[li]));
+        if (hc_sx && hs < 12) w = f2fma(f2(cu_sx), sc[li ^ (1 << hs)], w);
+        if (k > 0) w = f2fma(f2(-bk), sp[li], w);
+        acc_a = f2fma(v[j], w, acc_a);
+        acc_n = f2fma(w, w, acc_n);
+        acc_q = f2fma(v[j], v[j], acc_q);
+        W[cc][j] = w;
+        if (!last) stv(wdst + gi, w);
+      }
+    }
+    float acc[3] = {acc_a.x + acc_a.y, acc_n.x + acc_n.y, acc_q.x + acc_q.y};
+    double out[3];
+    if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
+    const double alpha = out[0];
+    const double b2 = out[1] - 2.0 * alpha * alpha + alpha * alpha * out[2];
+    double beta = sqrt(fmax(b2, 0.0));
+    if (!isfinite(alpha) || !isfinite(out[1])) {
+      if (tid == 0) { atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_NONFINITE); atomicExch(p.ctrl + kCtrlAbort, 1); }
+      return false;
+    }
+    if (!last && b2 < 1e-3 * out[1]) {  // near an invariant subspace: explicit ||W - alpha v||^2
+      float n1[1] = {0.f};
+      const float ra = (float)alpha;
+      for (int cc = 0; cc < n_own; ++cc) {
+        const float2* sc = s_cur + cc * T;
+#pragma unroll
+        for (int j = 0; j < APT; ++j) {
+          const float2 r = f2fma(f2(-ra), sc[tid + j * NT], W[cc][j]);
+          n1[0] += r.x * r.x + r.y * r.y;
+        }
+      }
+      double o1[1];
+      if (!group_reduce<1>(c.g, ss.red, n1, o1)) return false;
+      beta = sqrt(fmax(o1[0], 0.0));
+    }
+    if (tid == 0) ss.alpha[k] = alpha;
+    if (last) {
+      beta_m = beta;
+      break;
+    }
+    amax = fmax(amax, fabs(alpha));
+    if (beta <= p.bd_tol * fmax(1.0, amax + bmax)) {
+      meff = k + 1;
+      broke = true;
+      break;
+    }
+    bmax = fmax(bmax, beta);
+    if (tid == 0) ss.beta[k + 1] = beta;
+    a_prev = alpha;
+    b_cur = beta;
+  }
+  meff_out = meff;
+  broke_out = broke;
+  beta_m_out = beta_m;
+  return true;
+}
+
+// One Krylov step src -> dst (App. A): Lanczos basis, small exponential, recombination.
+// tau = sigma * dt.  Returns false on abort.
+template <class V, class A, int APT, int TPC, bool RES, bool FAST>
+__device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_src, double uj, double tau, V* dst,
+                                          int extra, const V* psi_other, double& nrm_dst, double2& e) {
+  int meff = 0;
+  bool broke = false;
+  double beta_m = 0.0;
+  bool ok;
+  if constexpr (FAST) ok = lanczos_res64(c, src, nrm_src, uj, meff, broke, beta_m);
+  else ok = lanczos_generic<V, A, APT, TPC, RES>(c, src, nrm_src, uj, meff, broke, beta_m);
+  if (!ok) return false;
+  return finish_slice<V, A, APT>(c, src, nrm_src, tau, meff, broke, beta_m, dst, extra, psi_other, nrm_dst, e);
+}
+
 // chi_N = beta f, ||chi_N||, and G_N = 2 dt Im <chi_N|Hc|psi_N>.
 template <class V>
 __device__ bool init_costate(Ctx<V>& c, double2 beta, V* chi, const V* psiN, double& nrm, double& gim) {
@@ -527,7 +757,7 @@ __device__ __forceinline__ V* fwd_slot(const Ctx<V>& c, int j) {
   return (V*)p.seg + (size_t)(C - 1 + (j & 1)) * c.D;
 }
 
-template <class V, class A, int APT, int TPC, bool RES>
+template <class V, class A, int APT, int TPC, bool RES, bool FAST>
 __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_constant__ EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
@@ -566,7 +796,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
     double nrm_new;
     double2 e;
     const int extra = (j == p.N) ? kExtraOverlapTarget : kExtraNone;
-    if (!krylov_slice<V, A, APT, TPC, RES>(c, fwd_slot<V>(c, j - 1), nrm_prev, p.u[j - 1], p.dt, fwd_slot<V>(c, j),
+    if (!krylov_slice<V, A, APT, TPC, RES, FAST>(c, fwd_slot<V>(c, j - 1), nrm_prev, p.u[j - 1], p.dt, fwd_slot<V>(c, j),
                                            extra, nullptr, nrm_new, e))
       return;
     if (lead) p.nrm[j] = nrm_new;
@@ -601,7 +831,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
           V* d = (V*)p.seg + (size_t)(i - a - 1) * c.D;
           double nn;
           double2 e;
-          if (!krylov_slice<V, A, APT, TPC, RES>(c, prev, np, p.u[i - 1], p.dt, d, kExtraNone, nullptr, nn, e))
+          if (!krylov_slice<V, A, APT, TPC, RES, FAST>(c, prev, np, p.u[i - 1], p.dt, d, kExtraNone, nullptr, nn, e))
             return;
           prev = d;
           np = nn;
@@ -614,7 +844,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
         else psi_jm1 = (V*)p.seg + (size_t)(j - 1 - a - 1) * c.D;
         double nn;
         double2 e;
-        if (!krylov_slice<V, A, APT, TPC, RES>(c, chi[cur], nchi, p.u[j - 1], -p.dt, chi[cur ^ 1],
+        if (!krylov_slice<V, A, APT, TPC, RES, FAST>(c, chi[cur], nchi, p.u[j - 1], -p.dt, chi[cur ^ 1],
                                                kExtraGradOverlap, psi_jm1, nn, e))
           return;
         if (lead) p.G[j - 1] = 2.0 * p.dt * e.x;
@@ -645,19 +875,21 @@ struct KernelChoice {
   size_t smem;
 };
 
-template <class V, class A, int APT, int TPC, bool RES>
+template <class V, class A, int APT, int TPC, bool RES, bool FAST>
 static KernelChoice choice(int t_bits) {
   constexpr int NB = RES ? TPC : 1;
-  return {(const void*)kg_eval_kernel<V, A, APT, TPC, RES>,
+  return {(const void*)kg_eval_kernel<V, A, APT, TPC, RES, FAST>,
           (size_t)(RES ? 3 : 2) * NB * ((size_t)1 << t_bits) * sizeof(V)};
 }
 
-// Variants: complex64 resident (<= 2 tiles of <= 4096 amplitudes per CTA), complex64
-// streaming, complex128 streaming (tiles of <= 2048 amplitudes).
+// Variants: complex64 resident with full 4096-amplitude tiles (specialised loop), complex64
+// resident (<= 2 tiles of <= 4096 amplitudes per CTA), complex64 streaming, complex128
+// streaming (tiles of <= 2048 amplitudes).
 static KernelChoice pick(int prec, int variant, int t_bits) {
-  if (prec == KG_PREC_C128) return choice<double2, double, 4, 1, false>(t_bits);
-  if (variant == kVariantResident) return choice<float2, float, 8, 2, true>(t_bits);
-  return choice<float2, float, 8, 1, false>(t_bits);
+  if (prec == KG_PREC_C128) return choice<double2, double, 4, 1, false, false>(t_bits);
+  if (variant == kVariantResidentFull) return choice<float2, float, 8, 2, true, true>(t_bits);
+  if (variant == kVariantResident) return choice<float2, float, 8, 2, true, false>(t_bits);
+  return choice<float2, float, 8, 1, false, false>(t_bits);
 }
 
 int max_tile_bits(int prec) { return prec == KG_PREC_C128 ? kLogNT + 2 : kLogNT + 3; }

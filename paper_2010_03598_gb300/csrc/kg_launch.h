@@ -9,7 +9,7 @@ namespace kg {
 
 constexpr int kThreads = 512;  // threads per CTA of the evaluation kernel
 
-enum { kVariantStreaming = 0, kVariantResident = 1 };
+enum { kVariantStreaming = 0, kVariantResident = 1, kVariantResidentFull = 2 };
 
 // Cooperative launch of the single-problem evaluation kernel (prec = kg_precision).
 cudaError_t launch_eval_kernel(int prec, int variant, const EvalParams& p, int ctas, cudaStream_t stream);
