@@ -76,9 +76,37 @@ struct Group {
 
 struct SmemRed {
   double warp_part[32 * kNRed];
+  float warp_part_f[32 * kNRed];
   double out[kNRed];
   int flag;
 };
+
+// ---------------------------------------------------------------- float-float sums
+// Error-free transformation of a float sum (Knuth's TwoSum): hi + lo == a + b exactly.
+// A float-float value carries ~48 significant bits, enough to add per-CTA partial sums
+// of the complex64 path without FP64 instructions (slow on this GPU) and without losing
+// accuracy to the number of CTAs.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const FF s = ff_two_sum(a.hi, b.hi);
+  const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s.hi, e);
+  return {hi, __fsub_rn(e, __fsub_rn(hi, s.hi))};
+}
+__device__ __forceinline__ FF ff_warp_sum(FF a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    a = ff_add(a, FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
+  return a;
+}
 
 // Barrier with a time limit.  Returns false (for every thread of the CTA) if the group
 // aborted or this CTA's wait ran past the limit; in the latter case it records
@@ -167,14 +195,59 @@ __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, A (&vals)[NV
   return true;
 }
 
+// Same contract for float per-thread values (complex64 path): warp sums in float, the CTA
+// partial and the sum over CTAs in float-float, one conversion to FP64 at the end.
+template <int NV>
+__device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, float (&vals)[NV], double (&out)[NV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
+  }
+  __syncthreads();
+  float2* slots = reinterpret_cast<float2*>(g.red + (size_t)(g.phase & 1) * kMaxCtas * kNRed);
+  g.phase++;
+  if (warp < NV) {
+    FF s{(lane < nw) ? sm.warp_part_f[lane * kNRed + warp] : 0.f, 0.f};
+    s = ff_warp_sum(s);
+    if (lane == 0) {
+      if (g.size > 1) __stcg(slots + (size_t)g.rank * kNRed + warp, make_float2(s.hi, s.lo));
+      else sm.out[warp] = (double)s.hi + (double)s.lo;
+    }
+  }
+  if (g.size > 1) {
+    if (!group_barrier(g, sm)) return false;
+    if (warp < NV) {
+      FF s{0.f, 0.f};
+      for (int r = lane; r < g.size; r += 32) {
+        const float2 q = __ldcg(slots + (size_t)r * kNRed + warp);
+        s = ff_add(s, FF{q.x, q.y});
+      }
+      s = ff_warp_sum(s);
+      if (lane == 0) sm.out[warp] = (double)s.hi + (double)s.lo;
+    }
+  } else if (ld_volatile_i32(g.ctrl + kCtrlAbort)) {
+    return false;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = sm.out[v];
+  return true;
+}
+
 // ---------------------------------------------------------------- small exponential
 // c = exp(-i tau T) e_1 for the real symmetric tridiagonal T of order n <= 32
 // (diag alpha[0..n-1], off-diagonal beta[1..n-1]; beta[k] couples k-1 and k),
-// executed by one full warp; lane k holds c_k.  Method: split tau into s equal steps
-// with ||(tau/s) T||_inf <= 1 (Gershgorin row sums) and sum the Taylor series of each
-// step until the remainder bound r^(K+1)/(K+1)! drops below 1e-18.  FP64 throughout.
-__device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const double* beta, int n,
-                                                double tau, double& c_re, double& c_im) {
+// executed by one full warp; lane k holds c_k.  Method: split tau into s equal steps with
+// ||(tau/s) T||_inf <= 1 (Gershgorin row sums); in each step sum the Taylor series
+// exp(-i h T) y = sum_p (-i h)^p T^p y / p!  until the remainder bound r^(K+1)/(K+1)!
+// drops below `tol`.  T is real, so for real y every term T^p y is real and (-i)^p only
+// picks the real or the imaginary part (and a sign); a complex y is two real series.
+// FP64 throughout.
+__device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const double* beta, int n, double tau,
+                                                double tol, double& c_re, double& c_im) {
   const int lane = threadIdx.x & 31;
   const bool in = lane < n;
   const double a = in ? alpha[lane] : 0.0;
@@ -185,27 +258,34 @@ __device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const doubl
   int s = (int)ceil(nrm);
   if (s < 1) s = 1;
   const double h = tau / (double)s;
-  // number of Taylor terms for radius r = nrm / s <= 1 (FP32 is enough to pick it)
-  const float r = (float)(nrm / (double)s);
+  const float r = (float)(nrm / (double)s);  // <= 1; FP32 is enough to pick the term count
   int K = 0;
   {
     float rem = r;  // r^(K+1) / (K+1)!, the first omitted term's bound
-    while (K < 30 && rem >= 1e-18f) { ++K; rem = rem * r / (float)(K + 1); }
+    while (K < 40 && rem >= (float)tol) { ++K; rem = rem * r / (float)(K + 1); }
   }
   double yr = (lane == 0) ? 1.0 : 0.0, yi = 0.0;
   for (int st = 0; st < s; ++st) {
-    double tr = yr, ti = yi, ar = yr, ai = yi;
+    const bool cplx = (st > 0);
+    double pr = yr, pi = yi;   // h^p T^p y / p!
+    double ar = yr, ai = yi;   // accumulated result
     for (int k = 1; k <= K; ++k) {
-      const double trm = __shfl_up_sync(0xffffffffu, tr, 1), tim = __shfl_up_sync(0xffffffffu, ti, 1);
-      const double trp = __shfl_down_sync(0xffffffffu, tr, 1), tip = __shfl_down_sync(0xffffffffu, ti, 1);
-      const double zr = fma(bl, trm, fma(a, tr, bh * trp));
-      const double zi = fma(bl, tim, fma(a, ti, bh * tip));
       const double f = h / (double)k;
-      // (-i f) (zr + i zi) = f zi - i f zr
-      tr = in ? f * zi : 0.0;
-      ti = in ? -f * zr : 0.0;
-      ar += tr;
-      ai += ti;
+      const double prm = __shfl_up_sync(0xffffffffu, pr, 1), prp = __shfl_down_sync(0xffffffffu, pr, 1);
+      pr = in ? f * fma(bl, prm, fma(a, pr, bh * prp)) : 0.0;
+      double pim = 0.0;
+      if (cplx) {
+        const double pim_ = __shfl_up_sync(0xffffffffu, pi, 1), pip = __shfl_down_sync(0xffffffffu, pi, 1);
+        pim = in ? f * fma(bl, pim_, fma(a, pi, bh * pip)) : 0.0;
+        pi = pim;
+      }
+      // (-i)^k: k%4 == 1 -> -i, 2 -> -1, 3 -> +i, 0 -> +1, applied to (pr + i pi)
+      switch (k & 3) {
+        case 0: ar += pr; ai += pi; break;
+        case 1: ar += pi; ai -= pr; break;
+        case 2: ar -= pr; ai -= pi; break;
+        default: ar -= pi; ai += pr; break;
+      }
     }
     yr = ar;
     yi = ai;

@@ -41,8 +41,85 @@ struct SmemSlice {
   double beta[kMaxM + 1];
   double coef_re[kMaxM];
   double coef_im[kMaxM];
+  float coef_re_f[kMaxM];
+  float coef_im_f[kMaxM];
   double err;
+  // scalars of the Lanczos recurrence, formed once per CTA by thread 0 and broadcast
+  double s_ap, s_ib, s_bk, s_alpha, s_b2, beta_m, nrm_out, s_ib0;
+  float f_ap, f_ib, f_bk, f_alpha, f_ib0;
+  int code1, stop, meff, broke;
 };
+
+template <class R> __device__ __forceinline__ R pick_r(double d, float f);
+template <> __device__ __forceinline__ float pick_r<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double pick_r<double>(double d, float) { return d; }
+
+// Thread 0: start of a slice's Lanczos loop with ||psi|| = nrm (alpha_{-1} = 0, b_0 = nrm).
+__device__ __forceinline__ void lz_init(SmemSlice& ss, double nrm, int m) {
+  const double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+  ss.s_ap = 0.0;
+  ss.s_ib = inv;
+  ss.s_bk = nrm;
+  ss.f_ap = 0.f;
+  ss.f_ib = (float)inv;
+  ss.f_bk = (float)nrm;
+  ss.s_ib0 = inv;
+  ss.f_ib0 = (float)inv;
+  ss.meff = (nrm > 0.0) ? m : 0;
+  ss.broke = 0;
+  ss.beta_m = 0.0;
+}
+
+// Thread 0, after the reduction of step k (out = <v|W>, ||W||^2, ||v||^2): alpha_k and
+// b_{k+1}^2 = ||W||^2 - 2 alpha <v|W> + alpha^2 ||v||^2.  code1: 0 go on, 1 the identity
+// cancels (near an invariant subspace: form ||W - alpha v||^2 explicitly), 2 non-finite.
+__device__ __forceinline__ void lz_after_reduce(SmemSlice& ss, int k, bool last, const double (&out)[3]) {
+  const double alpha = out[0];
+  ss.alpha[k] = alpha;
+  ss.s_alpha = alpha;
+  ss.f_alpha = (float)alpha;
+  ss.s_b2 = out[1] - 2.0 * alpha * alpha + alpha * alpha * out[2];
+  int code = 0;
+  if (!isfinite(alpha) || !isfinite(out[1])) code = 2;
+  else if (!last && ss.s_b2 < 1e-3 * out[1]) code = 1;
+  ss.code1 = code;
+}
+
+// Thread 0: b_{k+1}, the breakdown test of Alg. "Lanczos" (b_j > 0, with a tolerance), and
+// the scalars of step k+1.  stop = 1 after the last step or a breakdown.
+__device__ __forceinline__ void lz_finish_step(SmemSlice& ss, int k, bool last, double bd_tol, double& amax,
+                                               double& bmax) {
+  const double beta = sqrt(fmax(ss.s_b2, 0.0));
+  const double alpha = ss.s_alpha;
+  int stop = 0;
+  if (last) {
+    ss.beta_m = beta;
+    stop = 1;
+  } else {
+    amax = fmax(amax, fabs(alpha));
+    if (beta <= bd_tol * fmax(1.0, amax + bmax)) {
+      ss.meff = k + 1;
+      ss.broke = 1;
+      stop = 1;
+    } else {
+      bmax = fmax(bmax, beta);
+      ss.beta[k + 1] = beta;
+      const double inv = 1.0 / beta;
+      ss.s_ap = alpha;
+      ss.s_ib = inv;
+      ss.s_bk = beta;
+      ss.f_ap = (float)alpha;
+      ss.f_ib = (float)inv;
+      ss.f_bk = (float)beta;
+    }
+  }
+  ss.stop = stop;
+}
+
+__device__ __forceinline__ void flag_nonfinite(const EvalParams& p) {
+  atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_NONFINITE);
+  atomicExch(p.ctrl + kCtrlAbort, 1);
+}
 
 template <class V>
 struct Ctx {
@@ -168,8 +245,7 @@ __device__ __forceinline__ void apply_H_tile(const Ctx<V>& c, size_t base, const
 }
 
 template <class V, class A, int APT, int TPC, bool RES>
-__device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double nrm_src, double uj, int& meff_out,
-                                                bool& broke_out, double& beta_m_out) {
+__device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double nrm_src, double uj) {
   using R = typename VecTraits<V>::R;
   const EvalParams& p = *c.p;
   SmemSlice& ss = *c.ss;
@@ -182,24 +258,21 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
 
   V W[NB][APT];                    // W_k of the own amplitudes (k = 0: the source vector psi)
   V X[RES ? 1 : NB][RES ? 1 : APT];  // streaming: part of H v_k leaving the tile (resident: in c.sx)
-  int meff = 0;
-  bool broke = false;
-  double beta_m = 0.0;
-  double a_prev = 0.0, b_cur = nrm_src;  // alpha_{k-1}, b_k (b_0 = ||psi||)
-  double amax = 0.0, bmax = 0.0;
-
-  if (nrm_src > 0.0) {
-    meff = m;
+  double amax = 0.0, bmax = 0.0;     // thread 0: running maxima for the breakdown test
+  if (tid == 0) lz_init(ss, nrm_src, m);
+  __syncthreads();
+  if (ss.meff > 0) {
     for (int k = 0; k < m; ++k) {
       const bool last = (k == m - 1);
       const V* wsrc = (k == 0) ? src : c.wbuf(k);       // W_k (global, all tiles)
       V* wdst = last ? nullptr : c.wbuf(k + 1);          // W_{k+1}
       V* vslot = (k == 0) ? nullptr : c.basis_slot(k);  // v_k (normalised)
       const V* vprev_g = (k == 0) ? nullptr : ((k == 1) ? src : c.basis_slot(k - 1));
-      const R ap = (R)a_prev;
-      const R ib = (R)(1.0 / b_cur);
-      const R bk = (R)b_cur;
-      const R vprev_scale = (k == 1) ? (R)(1.0 / nrm_src) : (R)1;  // slot 0 is psi, unnormalised
+      const R ap = pick_r<R>(ss.s_ap, ss.f_ap);
+      const R ib = pick_r<R>(ss.s_ib, ss.f_ib);
+      const R bk = pick_r<R>(ss.s_bk, ss.f_bk);
+      // slot 0 is psi itself (unnormalised): v_0 = psi * (1 / b_0); ib of step 1 is 1 / b_1
+      const R vprev_scale = (k == 1) ? pick_r<R>(ss.s_ib0, ss.f_ib0) : (R)1;
       V* s_cur = c.sv[k & 1];
       V* s_prev = c.sv[(k & 1) ^ 1];
       A acc[3] = {0, 0, 0};
@@ -308,19 +381,18 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
       }
       double out[3];
       if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
-      const double alpha = out[0];
-      // ||W - alpha v||^2 = ||W||^2 - 2 alpha <v|W> + alpha^2 ||v||^2, with <v|W> = alpha
-      const double b2 = out[1] - 2.0 * alpha * alpha + alpha * alpha * out[2];
-      double beta = sqrt(fmax(b2, 0.0));
-      if (!isfinite(alpha) || !isfinite(out[1])) {
-        if (tid == 0) { atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_NONFINITE); atomicExch(p.ctrl + kCtrlAbort, 1); }
+      if (tid == 0) lz_after_reduce(ss, k, last, out);
+      __syncthreads();
+      const int code = ss.code1;
+      if (code == 2) {
+        if (tid == 0) flag_nonfinite(p);
         return false;
       }
-      if (!last && b2 < 1e-3 * out[1]) {
+      if (code == 1) {
         // Near an invariant subspace the identity loses the small b_{k+1} to cancellation:
         // form ||W_{k+1} - alpha_k v_k||^2 explicitly (one more reduction, rare).
         A n1[1] = {0};
-        const R ra = (R)alpha;
+        const R ra = pick_r<R>(ss.s_alpha, ss.f_alpha);
         for (int ct = 0; ct < c.n_own; ++ct) {
           const size_t base = c.tile_base(ct);
 #pragma unroll
@@ -337,56 +409,45 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
         }
         double o1[1];
         if (!group_reduce<1>(c.g, ss.red, n1, o1)) return false;
-        beta = sqrt(fmax(o1[0], 0.0));
+        if (tid == 0) ss.s_b2 = o1[0];
       }
-      if (tid == 0) ss.alpha[k] = alpha;
-      if (last) {
-        beta_m = beta;
-        break;
-      }
-      amax = fmax(amax, fabs(alpha));
-      if (beta <= p.bd_tol * fmax(1.0, amax + bmax)) {
-        meff = k + 1;
-        broke = true;
-        break;
-      }
-      bmax = fmax(bmax, beta);
-      if (tid == 0) ss.beta[k + 1] = beta;
-      a_prev = alpha;
-      b_cur = beta;
+      if (tid == 0) lz_finish_step(ss, k, last, p.bd_tol, amax, bmax);
+      __syncthreads();
+      if (ss.stop) break;
     }
   }
-  meff_out = meff;
-  broke_out = broke;
-  beta_m_out = beta_m;
   return true;
 }
 
 // Small exponential c = exp(-i tau T) e_1 and recombination dst = ||src|| sum_k c_k v_k of the
 // own tiles (App. A), with fused ||dst||^2 and the optional overlap:
-// extra == kExtraOverlapTarget: e = <f|dst> (f = target, complex128);
+// extra == kExtraOverlapTarget: e = <f|dst> (f = target, complex128, FP64 sums);
 // extra == kExtraGradOverlap:   e.x = Im <dst|Hc|psi_other>.
+// Reads meff, broke and b_m of the Lanczos loop from shared memory.
 template <class V, class A, int APT>
-__device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm_src, double tau, int meff, bool broke,
-                                             double beta_m, V* dst, int extra, const V* psi_other, double& nrm_dst,
-                                             double2& e) {
+__device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm_src, double tau, V* dst, int extra,
+                                             const V* psi_other, double& nrm_dst, double2& e) {
   using R = typename VecTraits<V>::R;
   const EvalParams& p = *c.p;
   SmemSlice& ss = *c.ss;
   const int tid = threadIdx.x;
   const int T = c.tile;
-  __syncthreads();
-  // ---- small exponential and recombination coefficients (warp 0)
+  const int meff = ss.meff;
+  // ---- small exponential and recombination coefficients (warp 0, FP64)
   if (tid < 32) {
+    const bool broke = ss.broke != 0;
     double cr = 0.0, ci = 0.0;
-    if (meff > 0) tridiag_expv_e1(ss.alpha, ss.beta, meff, tau, cr, ci);
+    const double tol = (sizeof(R) == 4) ? 1e-13 : 1e-18;
+    if (meff > 0) tridiag_expv_e1(ss.alpha, ss.beta, meff, tau, tol, cr, ci);
     if (tid < meff) {
       // basis slot 0 is psi itself (unnormalised); slots k >= 1 hold normalised v_k
       const double f = (tid == 0) ? 1.0 : nrm_src;
       ss.coef_re[tid] = cr * f;
       ss.coef_im[tid] = ci * f;
+      ss.coef_re_f[tid] = (float)(cr * f);
+      ss.coef_im_f[tid] = (float)(ci * f);
     }
-    if (tid == meff - 1 && meff > 0) {
+    if (tid == meff - 1) {
       // a-posteriori indicator nrm * b_m * |c_{m-1}|; where the Taylor series stopped before
       // reaching index m-1, |c_{m-1}| <= ||tau T||^(m-1) / (m-1)! bounds it instead
       double cm = sqrt(cr * cr + ci * ci);
@@ -397,17 +458,15 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
         cm = 1.0;
         for (int i = 1; i < meff; ++i) cm *= r / (double)i;
       }
-      ss.err = broke ? 0.0 : nrm_src * beta_m * cm;
+      ss.err = broke ? 0.0 : nrm_src * ss.beta_m * cm;
+      c.err_max = fmax(c.err_max, ss.err);  // lane meff-1 of warp 0 keeps the running maximum
     }
   }
   __syncthreads();
-  if (meff > 0 && tid == 0) {
-    c.err_max = fmax(c.err_max, ss.err);
-    c.breakdowns += broke ? 1 : 0;
-  }
+  if (tid == 0 && meff > 0) c.breakdowns += ss.broke ? 1 : 0;
   // ---- recombination dst = sum_k coef_k v_k (+ fused norms / overlaps)
-  A nacc[1] = {0};
-  double ex[2] = {0.0, 0.0};
+  A nacc = 0, gacc = 0;
+  double ex0 = 0.0, ex1 = 0.0;
   for (int ct = 0; ct < c.n_own; ++ct) {
     const size_t base = c.tile_base(ct);
     V y[APT];
@@ -415,7 +474,7 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
     for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
     for (int k = 0; k < meff; ++k) {
       const V* s = (k == 0) ? src : c.basis_slot(k);
-      const R a = (R)ss.coef_re[k], b = (R)ss.coef_im[k];
+      const R a = pick_r<R>(ss.coef_re[k], ss.coef_re_f[k]), b = pick_r<R>(ss.coef_im[k], ss.coef_im_f[k]);
       V q[APT];
 #pragma unroll
       for (int j = 0; j < APT; ++j) {
@@ -435,37 +494,52 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
       const size_t gi = base + li;
       const R yr = y[j].x, yi = y[j].y;
       stv(dst + gi, y[j]);
-      nacc[0] += (A)(yr * yr + yi * yi);
+      nacc += (A)(yr * yr + yi * yi);
       if (extra == kExtraOverlapTarget) {
         const double2 f = reinterpret_cast<const double2*>(p.target)[gi];
-        ex[0] += f.x * (double)yr + f.y * (double)yi;
-        ex[1] += f.x * (double)yi - f.y * (double)yr;
+        ex0 += f.x * (double)yr + f.y * (double)yi;
+        ex1 += f.x * (double)yi - f.y * (double)yr;
       } else if (extra == kExtraGradOverlap) {
         V q;
         if (p.hc_kind == KG_HC_SX_SITE) {
           q = ldv(psi_other + (gi ^ ((size_t)1 << p.hc_site)));
-          q.x *= (R)(0.5 * p.hc_amp);
-          q.y *= (R)(0.5 * p.hc_amp);
+          const R h = pick_r<R>(0.5 * p.hc_amp, 0.5f * (float)p.hc_amp);
+          q.x *= h;
+          q.y *= h;
         } else {
           const unsigned mk = (unsigned)p.hc_mask;
-          const R dz = (R)(p.hc_amp * 0.5 * (double)(__popc(mk) - 2 * __popc((unsigned)gi & mk)));
+          const int nz = __popc(mk) - 2 * __popc((unsigned)gi & mk);
+          const R dz = pick_r<R>(p.hc_amp * 0.5 * (double)nz, (float)p.hc_amp * 0.5f * (float)nz);
           q = ldv(psi_other + gi);
           q.x *= dz;
           q.y *= dz;
         }
-        ex[0] += (double)(yr * q.y - yi * q.x);  // Im(conj(y) q)
+        gacc += (A)(yr * q.y - yi * q.x);  // Im(conj(y) q)
       }
     }
   }
-  double out[3];
-  double vals[3] = {(double)nacc[0], ex[0], ex[1]};
-  if (!group_reduce<3>(c.g, ss.red, vals, out)) return false;
-  nrm_dst = sqrt(fmax(out[0], 0.0));
-  e = make_double2(out[1], out[2]);
-  if (!isfinite(out[0])) {
-    if (tid == 0) { atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_NONFINITE); atomicExch(p.ctrl + kCtrlAbort, 1); }
+  double out[3] = {0.0, 0.0, 0.0};
+  if (extra == kExtraOverlapTarget) {
+    double vals[3] = {(double)nacc, ex0, ex1};
+    if (!group_reduce<3>(c.g, ss.red, vals, out)) return false;
+  } else {
+    A vals[2] = {nacc, gacc};
+    double o2[2];
+    if (!group_reduce<2>(c.g, ss.red, vals, o2)) return false;
+    out[0] = o2[0];
+    out[1] = o2[1];
+  }
+  if (tid == 0) {
+    ss.nrm_out = sqrt(fmax(out[0], 0.0));
+    ss.code1 = isfinite(out[0]) ? 0 : 2;
+  }
+  __syncthreads();
+  if (ss.code1 == 2) {
+    if (tid == 0) flag_nonfinite(p);
     return false;
   }
+  nrm_dst = ss.nrm_out;
+  e = make_double2(out[1], out[2]);
   return true;
 }
 
@@ -482,8 +556,7 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return _
 //   bond 8      (bit 8 of tid, bit 0 of j): partner (tid ^ 256) + 512 (j ^ 1)
 //   bonds 9, 10 (bits of j):        partner in registers, test known at compile time
 //   bond 11 and up:                 other tiles (X recurrence, stage 1)
-__device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, double nrm_src, double uj,
-                                           int& meff_out, bool& broke_out, double& beta_m_out) {
+__device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, double nrm_src, double uj) {
   const EvalParams& p = *c.p;
   SmemSlice& ss = *c.ss;
   constexpr int APT = 8, NB = 2, T = 4096, NT = kThreads;
@@ -499,22 +572,16 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
   const int t8 = (tid >> 8) & 1;
   const int n_own = c.n_own;
   float2 W[NB][APT];
-  int meff = m;
-  bool broke = false;
-  double beta_m = 0.0;
-  double a_prev = 0.0, b_cur = nrm_src, amax = 0.0, bmax = 0.0;
-  if (!(nrm_src > 0.0)) {
-    meff_out = 0;
-    broke_out = false;
-    beta_m_out = 0.0;
-    return true;
-  }
+  double amax = 0.0, bmax = 0.0;  // thread 0: running maxima for the breakdown test
+  if (tid == 0) lz_init(ss, nrm_src, m);
+  __syncthreads();
+  if (ss.meff == 0) return true;
   for (int k = 0; k < m; ++k) {
     const bool last = (k == m - 1);
     const float2* wsrc = (k == 0) ? src : c.wbuf(k);
     float2* wdst = last ? nullptr : c.wbuf(k + 1);
     float2* vslot = (k == 0) ? nullptr : c.basis_slot(k);
-    const float ap = (float)a_prev, ib = (float)(1.0 / b_cur), bk = (float)b_cur;
+    const float ap = ss.f_ap, ib = ss.f_ib, bk = ss.f_bk;
     float2* s_cur = c.sv[k & 1];
     const float2* s_prev = c.sv[(k & 1) ^ 1];
     float2 acc_a = f2(0.f), acc_n = f2(0.f), acc_q = f2(0.f);
@@ -624,16 +691,16 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
     float acc[3] = {acc_a.x + acc_a.y, acc_n.x + acc_n.y, acc_q.x + acc_q.y};
     double out[3];
     if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
-    const double alpha = out[0];
-    const double b2 = out[1] - 2.0 * alpha * alpha + alpha * alpha * out[2];
-    double beta = sqrt(fmax(b2, 0.0));
-    if (!isfinite(alpha) || !isfinite(out[1])) {
-      if (tid == 0) { atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_NONFINITE); atomicExch(p.ctrl + kCtrlAbort, 1); }
+    if (tid == 0) lz_after_reduce(ss, k, last, out);
+    __syncthreads();
+    const int code = ss.code1;
+    if (code == 2) {
+      if (tid == 0) flag_nonfinite(p);
       return false;
     }
-    if (!last && b2 < 1e-3 * out[1]) {  // near an invariant subspace: explicit ||W - alpha v||^2
+    if (code == 1) {  // near an invariant subspace: explicit ||W - alpha v||^2
       float n1[1] = {0.f};
-      const float ra = (float)alpha;
+      const float ra = ss.f_alpha;
       for (int cc = 0; cc < n_own; ++cc) {
         const float2* sc = s_cur + cc * T;
 #pragma unroll
@@ -644,27 +711,12 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
       }
       double o1[1];
       if (!group_reduce<1>(c.g, ss.red, n1, o1)) return false;
-      beta = sqrt(fmax(o1[0], 0.0));
+      if (tid == 0) ss.s_b2 = o1[0];
     }
-    if (tid == 0) ss.alpha[k] = alpha;
-    if (last) {
-      beta_m = beta;
-      break;
-    }
-    amax = fmax(amax, fabs(alpha));
-    if (beta <= p.bd_tol * fmax(1.0, amax + bmax)) {
-      meff = k + 1;
-      broke = true;
-      break;
-    }
-    bmax = fmax(bmax, beta);
-    if (tid == 0) ss.beta[k + 1] = beta;
-    a_prev = alpha;
-    b_cur = beta;
+    if (tid == 0) lz_finish_step(ss, k, last, p.bd_tol, amax, bmax);
+    __syncthreads();
+    if (ss.stop) break;
   }
-  meff_out = meff;
-  broke_out = broke;
-  beta_m_out = beta_m;
   return true;
 }
 
@@ -673,14 +725,11 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
 template <class V, class A, int APT, int TPC, bool RES, bool FAST>
 __device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_src, double uj, double tau, V* dst,
                                           int extra, const V* psi_other, double& nrm_dst, double2& e) {
-  int meff = 0;
-  bool broke = false;
-  double beta_m = 0.0;
   bool ok;
-  if constexpr (FAST) ok = lanczos_res64(c, src, nrm_src, uj, meff, broke, beta_m);
-  else ok = lanczos_generic<V, A, APT, TPC, RES>(c, src, nrm_src, uj, meff, broke, beta_m);
+  if constexpr (FAST) ok = lanczos_res64(c, src, nrm_src, uj);
+  else ok = lanczos_generic<V, A, APT, TPC, RES>(c, src, nrm_src, uj);
   if (!ok) return false;
-  return finish_slice<V, A, APT>(c, src, nrm_src, tau, meff, broke, beta_m, dst, extra, psi_other, nrm_dst, e);
+  return finish_slice<V, A, APT>(c, src, nrm_src, tau, dst, extra, psi_other, nrm_dst, e);
 }
 
 // chi_N = beta f, ||chi_N||, and G_N = 2 dt Im <chi_N|Hc|psi_N>.
@@ -862,8 +911,9 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
         p.grad[j] = (p.grad_mode == KG_GRAD_ZEROTH) ? gr : 0.5 * (gl + gr);
       }
     }
+    double em = (threadIdx.x < 32) ? warp_max(c.err_max) : 0.0;
     if (threadIdx.x == 0) {
-      p.scal[kScErrMax] = c.err_max;
+      p.scal[kScErrMax] = em;
       p.scal[kScBreakdowns] = (double)c.breakdowns;
     }
   }
