@@ -99,6 +99,7 @@ typedef struct kg_options {
 } kg_options;
 
 #define KG_FLAG_HOST_STAGING 1u  /* reserve workspace for kg_evaluate_host's input/output copies */
+#define KG_FLAG_PHASE_TIMING 2u  /* record per-phase SM cycles of CTA 0 into kg_report.phase_cycles */
 
 /* Diagnostics of the last evaluation, filled by kg_sync. */
 typedef struct kg_report {
@@ -111,6 +112,12 @@ typedef struct kg_report {
   int32_t ctas;            /* CTAs that cooperated on the problem */
   int32_t tile_bits;       /* tile size used */
   int32_t threads;         /* threads per CTA */
+  int64_t phase_cycles[8]; /* with KG_FLAG_PHASE_TIMING: SM clock cycles CTA 0 spent in
+                              [0] Lanczos stage 1 (v_k, partners from other tiles),
+                              [1] stage 2 (stencil inside the tile), [2] group reductions
+                              incl. the barrier wait, [3] recurrence scalars and broadcast,
+                              [4] small exponential, [5] recombination, [6] sweep setup,
+                              [7] total; zeros otherwise */
 } kg_report;
 
 typedef struct kg_handle kg_handle;   /* opaque host object; owns no device memory */

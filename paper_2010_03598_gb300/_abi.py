@@ -14,6 +14,7 @@ KG_PREC_C128, KG_PREC_C64_F64REC = 0, 1
 KG_GRAD_NONE, KG_GRAD_CENTERED, KG_GRAD_ZEROTH = 0, 1, 2
 KG_HC_SX_SITE, KG_HC_SZ_SITES = 0, 1
 KG_FLAG_HOST_STAGING = 1
+KG_FLAG_PHASE_TIMING = 2
 
 
 class KgChain(ctypes.Structure):
@@ -32,7 +33,7 @@ class KgReport(ctypes.Structure):
     _fields_ = [("krylov_err_max", ctypes.c_double), ("norm_final", ctypes.c_double), ("beta_re", ctypes.c_double),
                 ("beta_im", ctypes.c_double), ("breakdowns", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("ctas", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
-                ("threads", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 8)]
 
 
 _P = ctypes.c_void_p

@@ -47,10 +47,12 @@ class Options:
     tile_bits: int = 0
     ctas: int = 0
     host_staging: bool = False
+    phase_timing: bool = False
     breakdown_tol: float = 0.0
 
     def to_c(self) -> _abi.KgOptions:
-        flags = _abi.KG_FLAG_HOST_STAGING if self.host_staging else 0
+        flags = (_abi.KG_FLAG_HOST_STAGING if self.host_staging else 0) | \
+            (_abi.KG_FLAG_PHASE_TIMING if self.phase_timing else 0)
         return _abi.KgOptions(self.N, self.m, _PREC[self.prec], _GRAD[self.grad], self.ckpt_every, self.tile_bits,
                               self.ctas, flags, self.dt, self.breakdown_tol)
 
@@ -147,7 +149,9 @@ class KGrape:
         rep = _abi.KgReport()
         with torch.cuda.device(self.device):
             check(lib().kg_sync(self._h, ctypes.byref(rep)), "kg_sync")
-        return {f: getattr(rep, f) for f, _ in rep._fields_}
+        out = {f: getattr(rep, f) for f, _ in rep._fields_}
+        out["phase_cycles"] = list(rep.phase_cycles)
+        return out
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -30,7 +30,7 @@ kg_status cuda_fail(cudaError_t e, const char* what) {
 size_t align_up(size_t x) { return (x + kg::kAlign - 1) / kg::kAlign * kg::kAlign; }
 
 struct Layout {
-  size_t ctrl = 0, bar = 0, red = 0, scal = 0, G = 0, nrm = 0;
+  size_t ctrl = 0, bar = 0, red = 0, scal = 0, G = 0, nrm = 0, prof = 0;
   size_t basis = 0, traj = 0, seg = 0, chi = 0, wbuf = 0, xbuf = 0;
   size_t st_u = 0, st_psi0 = 0, st_target = 0, st_fid = 0, st_grad = 0;
   size_t total = 0;
@@ -60,7 +60,8 @@ kg_status check_args(const kg_chain* ch, const kg_options* o) {
   if (o->tile_bits != 0 && (o->tile_bits < 1 || o->tile_bits > 13))
     return fail(KG_ERR_INVALID_ARG, "tile_bits must be 0 (auto) or 1..13");
   if (o->ctas < 0 || o->ctas > kg::kMaxCtas) return fail(KG_ERR_INVALID_ARG, "ctas must be 0 (auto) or 1..2048");
-  if ((o->flags & ~KG_FLAG_HOST_STAGING) != 0) return fail(KG_ERR_INVALID_ARG, "unknown flag bits");
+  if ((o->flags & ~(KG_FLAG_HOST_STAGING | KG_FLAG_PHASE_TIMING)) != 0)
+    return fail(KG_ERR_INVALID_ARG, "unknown flag bits");
   if (!(o->dt > 0.0) || !std::isfinite(o->dt)) return fail(KG_ERR_INVALID_ARG, "dt must be finite and > 0");
   if (std::isnan(o->breakdown_tol)) return fail(KG_ERR_INVALID_ARG, "breakdown_tol must not be NaN");
   return KG_OK;
@@ -81,6 +82,7 @@ Layout make_layout(const kg_chain* ch, const kg_options* o) {
   l.bar = l.ctrl + 32;
   l.red = take(sizeof(double) * 2 * kg::kMaxCtas * kg::kNRed);
   l.scal = take(sizeof(double) * kg::kScCount);
+  l.prof = take(sizeof(long long) * 8);
   l.G = take(sizeof(double) * (size_t)(o->N + 1));
   l.nrm = take(sizeof(double) * (size_t)(o->N + 1));
   l.basis = take(vb * (size_t)(o->m > 1 ? o->m - 1 : 1));
@@ -177,7 +179,8 @@ kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options*
     int maxr = 0;
     e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantResident, t, &maxr);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    int c = (opts->ctas > 0) ? opts->ctas : ntiles;
+    // default: two tiles per CTA (paired so that every CTA has the same cross-tile work)
+    int c = (opts->ctas > 0) ? opts->ctas : (ntiles >= 2 ? ntiles / 2 : 1);
     if (c > ntiles) c = ntiles;
     if (c > maxr) c = maxr;
     if (c > kg::kMaxCtas) c = kg::kMaxCtas;
@@ -251,6 +254,7 @@ static kg_status enqueue(kg_handle* h, const double* u, const void* psi0, const 
   p.ctrl = (int*)(ws + h->lay.ctrl);
   p.wait_limit_ns = g_wait_limit_ns.load();
   p.debug_fault = g_debug_fault.exchange(0);
+  p.prof = (o.flags & KG_FLAG_PHASE_TIMING) ? (long long*)(ws + h->lay.prof) : nullptr;
   cudaError_t e = cudaMemsetAsync(ws + h->lay.ctrl, 0, 64, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(control block)");
   e = kg::launch_eval_kernel(o.prec, h->variant, p, h->ctas, h->stream);
@@ -294,6 +298,12 @@ kg_status kg_sync(kg_handle* h, kg_report* rep) {
     rep->ctas = h->ctas;
     rep->tile_bits = h->t_bits;
     rep->threads = kg::kThreads;
+    long long pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (h->opts.flags & KG_FLAG_PHASE_TIMING) {
+      e = cudaMemcpy(pc, h->ws + h->lay.prof, sizeof(pc), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(phase timing)");
+    }
+    for (int i = 0; i < 8; ++i) rep->phase_cycles[i] = pc[i];
   }
   const int st = ctrl[kg::kCtrlStatus];
   if (st == KG_ERR_TIMEOUT) return fail(KG_ERR_TIMEOUT, "a device-side wait ran past its time limit");

@@ -59,6 +59,36 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// ---------------------------------------------------------------- bulk copies (TMA)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// Arrive on the barrier and announce `bytes` of asynchronous transactions for this phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global to shared
+// memory, completing as transactions on `bar`.
+__device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem, uint32_t bytes,
+                                            unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst_smem)),
+               "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 // ---------------------------------------------------------------- group context
 // A group is the set of CTAs that cooperate on one problem.  All CTAs of a group are
 // co-resident (cooperative launch), execute the same sequence of barriers/reductions,
@@ -238,27 +268,51 @@ __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, float (&vals
 }
 
 // ---------------------------------------------------------------- small exponential
+// 1/p! for p = 0..40 (exact rationals rounded once by the compiler).
+__device__ __constant__ double kInvFact[41] = {
+    1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320, 1.0 / 362880,
+    1.0 / 3628800.0, 1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0, 1.0 / 87178291200.0,
+    1.0 / 1307674368000.0, 1.0 / 20922789888000.0, 1.0 / 355687428096000.0, 1.0 / 6402373705728000.0,
+    1.0 / 121645100408832000.0, 1.0 / 2432902008176640000.0, 1.0 / 51090942171709440000.0,
+    1.0 / 1124000727777607680000.0, 1.0 / 25852016738884976640000.0, 1.0 / 620448401733239439360000.0,
+    1.0 / 15511210043330985984000000.0, 1.0 / 403291461126605635584000000.0,
+    1.0 / 10888869450418352160768000000.0, 1.0 / 304888344611713860501504000000.0,
+    1.0 / 8841761993739701954543616000000.0, 1.0 / 265252859812191058636308480000000.0,
+    1.0 / 8222838654177922817725562880000000.0, 1.0 / 263130836933693530167218012160000000.0,
+    1.0 / 8683317618811886495518194401280000000.0, 1.0 / 295232799039604140847618609643520000000.0,
+    1.0 / 10333147966386144929666651337523200000000.0, 1.0 / 371993326789901217467999448150835200000000.0,
+    1.0 / 13763753091226345046315979581580902400000000.0, 1.0 / 523022617466601111760007224100074291200000000.0,
+    1.0 / 20397882081197443358640281739902897356800000000.0,
+    1.0 / 815915283247897734345611269596115894272000000000.0};
+
 // c = exp(-i tau T) e_1 for the real symmetric tridiagonal T of order n <= 32
 // (diag alpha[0..n-1], off-diagonal beta[1..n-1]; beta[k] couples k-1 and k),
 // executed by one full warp; lane k holds c_k.  Method: split tau into s equal steps with
-// ||(tau/s) T||_inf <= 1 (Gershgorin row sums); in each step sum the Taylor series
-// exp(-i h T) y = sum_p (-i h)^p T^p y / p!  until the remainder bound r^(K+1)/(K+1)!
-// drops below `tol`.  T is real, so for real y every term T^p y is real and (-i)^p only
-// picks the real or the imaginary part (and a sign); a complex y is two real series.
-// FP64 throughout.
-__device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const double* beta, int n, double tau,
-                                                double tol, double& c_re, double& c_im) {
+// ||(tau/s) T||_inf <= 1 (Gershgorin row sums) and, with A = (tau/s) T, sum the Taylor
+// series exp(-i A) y = sum_p (-i)^p A^p y / p!  until the remainder bound r^(K+1)/(K+1)!
+// drops below `tol`.  A is real, so for real y every A^p y is real and (-i)^p only picks
+// the real or the imaginary part and a sign; a complex y is two real series.  ||A|| <= 1
+// keeps A^p y bounded.  FP64 throughout (about four FP64 operations per term and part).
+__device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const double* beta, const float* alpha_f,
+                                                const float* beta_f, int n, double tau, float tau_f, double tol,
+                                                double& c_re, double& c_im, float& tnorm) {
   const int lane = threadIdx.x & 31;
   const bool in = lane < n;
   const double a = in ? alpha[lane] : 0.0;
   const double bl = (in && lane >= 1) ? beta[lane] : 0.0;
   const double bh = (lane + 1 < n) ? beta[lane + 1] : 0.0;
-  const double row = fabs(tau) * (fabs(a) + fabs(bl) + fabs(bh));
-  const double nrm = warp_max(row);
-  int s = (int)ceil(nrm);
+  // Gershgorin bound of ||tau T||_inf and the step count in FP32 (a bound needs no more)
+  float row = 0.f;
+  if (in) row = fabsf(tau_f) * (fabsf(alpha_f[lane]) + (lane >= 1 ? beta_f[lane] : 0.f) +
+                                (lane + 1 < n ? beta_f[lane + 1] : 0.f));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) row = fmaxf(row, __shfl_xor_sync(0xffffffffu, row, o));
+  tnorm = row;
+  int s = (int)ceilf(row * 1.0001f);
   if (s < 1) s = 1;
-  const double h = tau / (double)s;
-  const float r = (float)(nrm / (double)s);  // <= 1; FP32 is enough to pick the term count
+  const double h = (s == 1) ? tau : tau / (double)s;
+  const double ha = h * a, hbl = h * bl, hbh = h * bh;  // rows of A = h T
+  const float r = row * 1.0001f / (float)s;             // <= 1 bound of ||A||
   int K = 0;
   {
     float rem = r;  // r^(K+1) / (K+1)!, the first omitted term's bound
@@ -267,24 +321,22 @@ __device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const doubl
   double yr = (lane == 0) ? 1.0 : 0.0, yi = 0.0;
   for (int st = 0; st < s; ++st) {
     const bool cplx = (st > 0);
-    double pr = yr, pi = yi;   // h^p T^p y / p!
-    double ar = yr, ai = yi;   // accumulated result
+    double pr = yr, pi = yi;  // A^p y
+    double ar = yr, ai = yi;  // accumulated result
     for (int k = 1; k <= K; ++k) {
-      const double f = h / (double)k;
       const double prm = __shfl_up_sync(0xffffffffu, pr, 1), prp = __shfl_down_sync(0xffffffffu, pr, 1);
-      pr = in ? f * fma(bl, prm, fma(a, pr, bh * prp)) : 0.0;
-      double pim = 0.0;
+      pr = fma(hbl, prm, fma(ha, pr, hbh * prp));
       if (cplx) {
-        const double pim_ = __shfl_up_sync(0xffffffffu, pi, 1), pip = __shfl_down_sync(0xffffffffu, pi, 1);
-        pim = in ? f * fma(bl, pim_, fma(a, pi, bh * pip)) : 0.0;
-        pi = pim;
+        const double pim = __shfl_up_sync(0xffffffffu, pi, 1), pip = __shfl_down_sync(0xffffffffu, pi, 1);
+        pi = fma(hbl, pim, fma(ha, pi, hbh * pip));
       }
+      const double w = kInvFact[k];
       // (-i)^k: k%4 == 1 -> -i, 2 -> -1, 3 -> +i, 0 -> +1, applied to (pr + i pi)
       switch (k & 3) {
-        case 0: ar += pr; ai += pi; break;
-        case 1: ar += pi; ai -= pr; break;
-        case 2: ar -= pr; ai -= pi; break;
-        default: ar -= pi; ai += pr; break;
+        case 0: ar = fma(w, pr, ar); if (cplx) ai = fma(w, pi, ai); break;
+        case 1: if (cplx) ar = fma(w, pi, ar); ai = fma(-w, pr, ai); break;
+        case 2: ar = fma(-w, pr, ar); if (cplx) ai = fma(-w, pi, ai); break;
+        default: if (cplx) ar = fma(-w, pi, ar); ai = fma(w, pr, ai); break;
       }
     }
     yr = ar;

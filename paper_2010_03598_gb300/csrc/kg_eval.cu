@@ -43,11 +43,14 @@ struct SmemSlice {
   double coef_im[kMaxM];
   float coef_re_f[kMaxM];
   float coef_im_f[kMaxM];
+  float alpha_f[kMaxM];
+  float beta_f[kMaxM + 1];
   double err;
   // scalars of the Lanczos recurrence, formed once per CTA by thread 0 and broadcast
   double s_ap, s_ib, s_bk, s_alpha, s_b2, beta_m, nrm_out, s_ib0;
-  float f_ap, f_ib, f_bk, f_alpha, f_ib0;
+  float f_ap, f_ib, f_bk, f_alpha, f_ib0, f_bk0, f_beta_m;
   int code1, stop, meff, broke;
+  unsigned long long mbar[4];  // bulk-copy ring of the recombination (resident complex64 path)
 };
 
 template <class R> __device__ __forceinline__ R pick_r(double d, float f);
@@ -65,6 +68,8 @@ __device__ __forceinline__ void lz_init(SmemSlice& ss, double nrm, int m) {
   ss.f_bk = (float)nrm;
   ss.s_ib0 = inv;
   ss.f_ib0 = (float)inv;
+  ss.f_bk0 = ss.f_bk;
+  ss.f_beta_m = 0.f;
   ss.meff = (nrm > 0.0) ? m : 0;
   ss.broke = 0;
   ss.beta_m = 0.0;
@@ -78,6 +83,7 @@ __device__ __forceinline__ void lz_after_reduce(SmemSlice& ss, int k, bool last,
   ss.alpha[k] = alpha;
   ss.s_alpha = alpha;
   ss.f_alpha = (float)alpha;
+  ss.alpha_f[k] = ss.f_alpha;
   ss.s_b2 = out[1] - 2.0 * alpha * alpha + alpha * alpha * out[2];
   int code = 0;
   if (!isfinite(alpha) || !isfinite(out[1])) code = 2;
@@ -89,11 +95,14 @@ __device__ __forceinline__ void lz_after_reduce(SmemSlice& ss, int k, bool last,
 // the scalars of step k+1.  stop = 1 after the last step or a breakdown.
 __device__ __forceinline__ void lz_finish_step(SmemSlice& ss, int k, bool last, double bd_tol, double& amax,
                                                double& bmax) {
-  const double beta = sqrt(fmax(ss.s_b2, 0.0));
+  const double b2 = fmax(ss.s_b2, 0.0);
+  const double rb = (b2 > 0.0) ? rsqrt(b2) : 0.0;  // 1 / b_{k+1}
+  const double beta = b2 * rb;
   const double alpha = ss.s_alpha;
   int stop = 0;
   if (last) {
     ss.beta_m = beta;
+    ss.f_beta_m = (float)beta;
     stop = 1;
   } else {
     amax = fmax(amax, fabs(alpha));
@@ -104,13 +113,14 @@ __device__ __forceinline__ void lz_finish_step(SmemSlice& ss, int k, bool last, 
     } else {
       bmax = fmax(bmax, beta);
       ss.beta[k + 1] = beta;
-      const double inv = 1.0 / beta;
+      const double inv = rb;
       ss.s_ap = alpha;
       ss.s_ib = inv;
       ss.s_bk = beta;
       ss.f_ap = (float)alpha;
       ss.f_ib = (float)inv;
       ss.f_bk = (float)beta;
+      ss.beta_f[k + 1] = ss.f_bk;
     }
   }
   ss.stop = stop;
@@ -119,6 +129,25 @@ __device__ __forceinline__ void lz_finish_step(SmemSlice& ss, int k, bool last, 
 __device__ __forceinline__ void flag_nonfinite(const EvalParams& p) {
   atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_NONFINITE);
   atomicExch(p.ctrl + kCtrlAbort, 1);
+}
+
+// Wait for phase `parity` of a bulk-copy barrier, at most `limit_ns`; false on time-out (the
+// status word then holds KG_ERR_TIMEOUT and the group is told to stop).
+__device__ __forceinline__ bool mbar_wait_bounded(const EvalParams& p, unsigned long long* bar, uint32_t parity) {
+  unsigned long long t0 = 0;
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      const unsigned long long now = globaltimer_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if ((long long)(now - t0) > p.wait_limit_ns) {
+        atomicCAS(p.ctrl + kCtrlStatus, 0, (int)KG_ERR_TIMEOUT);
+        atomicExch(p.ctrl + kCtrlAbort, 1);
+        return false;
+      }
+    }
+  }
 }
 
 template <class V>
@@ -130,14 +159,36 @@ struct Ctx {
   V* sv[2];         // shared memory: v_k and v_{k-1} of the own tiles ([TPC][tile] each)
   V* sx;            // shared memory (resident variant): X of the own tiles ([TPC][tile])
   int t, tile, ntiles, n_own;
+  bool paired;      // size == ntiles/2: CTA r owns tiles 2r and 2r ^ alt (equal cross-tile work)
+  unsigned alt;     // alternating bits 0, 2, 4, ... of the tile index
   size_t D;
   unsigned maskL1;  // bonds 0..L-2 in (i ^ i>>1)
   double err_max;
   int breakdowns;
+  unsigned ring_count;   // bulk-copy chunks consumed so far (ring stage and phase parity)
+  bool prof_on;          // phase timing (CTA 0, thread 0)
+  long long prof_last;
+  long long prof_acc[8];
 
+  __device__ __forceinline__ void mark(int phase) {
+    if (prof_on && threadIdx.x == 0) {
+      const long long now = clock64();
+      prof_acc[phase] += now - prof_last;
+      prof_last = now;
+    }
+  }
   __device__ V* basis_slot(int k) const { return (V*)p->basis + (size_t)(k - 1) * D; }
   __device__ V* wbuf(int k) const { return (V*)p->wbuf + (size_t)(k & 1) * D; }
-  __device__ size_t tile_base(int c) const { return (size_t)(g.rank + c * g.size) << t; }
+  // Tile owned as number c.  Paired: flipping every other tile-index bit toggles whether
+  // each adjacent pair of tile bits differs, so the two tiles of a CTA together have the
+  // same number of tile-uniform antiparallel bonds (cross-tile partner tiles) as any other pair.
+  __device__ size_t tile_base(int c) const {
+    if (paired) {
+      const unsigned T0 = 2u * (unsigned)g.rank;
+      return (size_t)(c == 0 ? T0 : (T0 ^ alt)) << t;
+    }
+    return (size_t)(g.rank + c * g.size) << t;
+  }
 };
 
 template <class V>
@@ -337,6 +388,7 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
           }
         }
         __syncthreads();
+        c.mark(0);
         // ---- stage 2: H v_k, W_{k+1} = H v_k - b_k v_{k-1}, partial sums
 #pragma unroll
         for (int cc = 0; cc < NB; ++cc) {
@@ -379,8 +431,10 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
         }
         if (!RES) __syncthreads();
       }
+      c.mark(1);
       double out[3];
       if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
+      c.mark(2);
       if (tid == 0) lz_after_reduce(ss, k, last, out);
       __syncthreads();
       const int code = ss.code1;
@@ -413,10 +467,51 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
       }
       if (tid == 0) lz_finish_step(ss, k, last, p.bd_tol, amax, bmax);
       __syncthreads();
+      c.mark(3);
       if (ss.stop) break;
     }
   }
   return true;
+}
+
+// Store the recombined amplitudes y of one tile and add their contributions to ||dst||^2 and
+// to the fused overlap (see finish_slice).
+template <class V, class A, int APT>
+__device__ __forceinline__ void recomb_finalize(const Ctx<V>& c, size_t base, const V (&y)[APT], V* dst, int extra,
+                                                const V* psi_other, A& nacc, A& gacc, double& ex0, double& ex1) {
+  using R = typename VecTraits<V>::R;
+  const EvalParams& p = *c.p;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < APT; ++j) {
+    const int li = tid + j * kThreads;
+    if (li >= c.tile) continue;
+    const size_t gi = base + li;
+    const R yr = y[j].x, yi = y[j].y;
+    stv(dst + gi, y[j]);
+    nacc += (A)(yr * yr + yi * yi);
+    if (extra == kExtraOverlapTarget) {
+      const double2 f = reinterpret_cast<const double2*>(p.target)[gi];
+      ex0 += f.x * (double)yr + f.y * (double)yi;
+      ex1 += f.x * (double)yi - f.y * (double)yr;
+    } else if (extra == kExtraGradOverlap) {
+      V q;
+      if (p.hc_kind == KG_HC_SX_SITE) {
+        q = ldv(psi_other + (gi ^ ((size_t)1 << p.hc_site)));
+        const R h = pick_r<R>(0.5 * p.hc_amp, 0.5f * (float)p.hc_amp);
+        q.x *= h;
+        q.y *= h;
+      } else {
+        const unsigned mk = (unsigned)p.hc_mask;
+        const int nz = __popc(mk) - 2 * __popc((unsigned)gi & mk);
+        const R dz = pick_r<R>(p.hc_amp * 0.5 * (double)nz, (float)p.hc_amp * 0.5f * (float)nz);
+        q = ldv(psi_other + gi);
+        q.x *= dz;
+        q.y *= dz;
+      }
+      gacc += (A)(yr * q.y - yi * q.x);  // Im(conj(y) q)
+    }
+  }
 }
 
 // Small exponential c = exp(-i tau T) e_1 and recombination dst = ||src|| sum_k c_k v_k of the
@@ -424,7 +519,7 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
 // extra == kExtraOverlapTarget: e = <f|dst> (f = target, complex128, FP64 sums);
 // extra == kExtraGradOverlap:   e.x = Im <dst|Hc|psi_other>.
 // Reads meff, broke and b_m of the Lanczos loop from shared memory.
-template <class V, class A, int APT>
+template <class V, class A, int APT, bool WBASIS>
 __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm_src, double tau, V* dst, int extra,
                                              const V* psi_other, double& nrm_dst, double2& e) {
   using R = typename VecTraits<V>::R;
@@ -437,8 +532,10 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
   if (tid < 32) {
     const bool broke = ss.broke != 0;
     double cr = 0.0, ci = 0.0;
+    float tnorm = 0.f;
     const double tol = (sizeof(R) == 4) ? 1e-13 : 1e-18;
-    if (meff > 0) tridiag_expv_e1(ss.alpha, ss.beta, meff, tau, tol, cr, ci);
+    if (meff > 0)
+      tridiag_expv_e1(ss.alpha, ss.beta, ss.alpha_f, ss.beta_f, meff, tau, (float)tau, tol, cr, ci, tnorm);
     if (tid < meff) {
       // basis slot 0 is psi itself (unnormalised); slots k >= 1 hold normalised v_k
       const double f = (tid == 0) ? 1.0 : nrm_src;
@@ -448,74 +545,149 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
       ss.coef_im_f[tid] = (float)(ci * f);
     }
     if (tid == meff - 1) {
-      // a-posteriori indicator nrm * b_m * |c_{m-1}|; where the Taylor series stopped before
-      // reaching index m-1, |c_{m-1}| <= ||tau T||^(m-1) / (m-1)! bounds it instead
-      double cm = sqrt(cr * cr + ci * ci);
-      if (cm == 0.0 && !broke) {
-        double r = 0.0;
-        for (int i = 0; i < meff; ++i)
-          r = fmax(r, fabs(tau) * (fabs(ss.alpha[i]) + (i > 0 ? ss.beta[i] : 0.0) + (i + 1 < meff ? ss.beta[i + 1] : 0.0)));
-        cm = 1.0;
-        for (int i = 1; i < meff; ++i) cm *= r / (double)i;
+      // a-posteriori indicator ||psi|| b_m |c_{m-1}| (= b_m |coef_{m-1}| for m > 1), in FP32;
+      // where the Taylor series stopped before index m-1, ||psi|| b_m ||tau T||^(m-1)/(m-1)!
+      // bounds it instead
+      float cm = sqrtf(ss.coef_re_f[tid] * ss.coef_re_f[tid] + ss.coef_im_f[tid] * ss.coef_im_f[tid]);
+      if (tid == 0) cm *= ss.f_bk0;
+      if (cm == 0.f && !broke) {
+        cm = ss.f_bk0;
+        for (int i = 1; i < meff; ++i) cm *= tnorm / (float)i;
       }
-      ss.err = broke ? 0.0 : nrm_src * ss.beta_m * cm;
-      c.err_max = fmax(c.err_max, ss.err);  // lane meff-1 of warp 0 keeps the running maximum
+      const float err = broke ? 0.f : ss.f_beta_m * cm;
+      c.err_max = fmax(c.err_max, (double)err);  // lane meff-1 of warp 0 keeps the running maximum
+    }
+    if constexpr (WBASIS) {
+      // Slots k >= 1 hold W_k with v_k = (W_k - alpha_{k-1} v_{k-1}) / b_k, v_0 = psi/||psi||:
+      // ||psi|| sum_k c_k v_k = sum_k e_k W_k + (s_0/||psi||) psi, where, from the top,
+      // s_{m-1} = ||psi|| c_{m-1}, e_k = s_k / b_k, s_{k-1} = ||psi|| c_{k-1} - e_k alpha_{k-1}.
+      // FP32 suffices: the coefficients only combine complex64 vectors.
+      __syncwarp();
+      if (tid == 0 && meff > 1) {
+        float sr = ss.coef_re_f[meff - 1], si = ss.coef_im_f[meff - 1];  // s_{m-1} = ||psi|| c_{m-1}
+        for (int k = meff - 1; k >= 2; --k) {
+          const float ib = 1.f / ss.beta_f[k], al = ss.alpha_f[k - 1];
+          const float er = sr * ib, ei = si * ib;
+          ss.coef_re_f[k] = er;
+          ss.coef_im_f[k] = ei;
+          sr = ss.coef_re_f[k - 1] - er * al;  // ||psi|| c_{k-1} - e_k alpha_{k-1}
+          si = ss.coef_im_f[k - 1] - ei * al;
+        }
+        const float ib = 1.f / ss.beta_f[1], al = ss.alpha_f[0];
+        const float er = sr * ib, ei = si * ib;  // e_1
+        ss.coef_re_f[1] = er;
+        ss.coef_im_f[1] = ei;
+        // psi coefficient s_0 / ||psi|| = c_0 - e_1 alpha_0 / ||psi|| (slot 0 held c_0)
+        ss.coef_re_f[0] -= er * al * ss.f_ib0;
+        ss.coef_im_f[0] -= ei * al * ss.f_ib0;
+      }
     }
   }
   __syncthreads();
+  c.mark(4);
   if (tid == 0 && meff > 0) c.breakdowns += ss.broke ? 1 : 0;
-  // ---- recombination dst = sum_k coef_k v_k (+ fused norms / overlaps)
+  // ---- recombination dst = sum_k coef_k (basis slot k) (+ fused norms / overlaps)
   A nacc = 0, gacc = 0;
   double ex0 = 0.0, ex1 = 0.0;
-  for (int ct = 0; ct < c.n_own; ++ct) {
-    const size_t base = c.tile_base(ct);
+  if constexpr (WBASIS) {
+    // Complex64 resident path: stream the own tiles of the basis through a 4-stage ring of
+    // 32 KB bulk copies (TMA) in the now idle shared memory; one chunk = one tile of one
+    // basis vector.  Thread 0 issues, every thread waits on the chunk's barrier phase.
+    constexpr int NS = 4;
+    constexpr uint32_t kChunk = 4096u * (uint32_t)sizeof(float2);
+    V* ring = c.sv[0];
+    const int nch = c.n_own * meff;
+    const unsigned g0 = c.ring_count;
+    fence_proxy_async();  // earlier generic-proxy writes (basis, psi, ring area) before bulk copies
+    __syncthreads();
+    auto chunk_src = [&](int i) -> const V* {
+      const int ct = i / meff, k = i - (i / meff) * meff;
+      return ((k == 0) ? src : c.basis_slot(k)) + c.tile_base(ct);
+    };
+    if (tid == 0) {
+      for (int i = 0; i < nch && i < NS; ++i) {
+        const unsigned st = (g0 + (unsigned)i) % NS;
+        mbar_arrive_expect_tx(&ss.mbar[st], kChunk);
+        tma_load_1d(ring + (size_t)st * 4096, chunk_src(i), kChunk, &ss.mbar[st]);
+      }
+    }
     V y[APT];
 #pragma unroll
     for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
-    for (int k = 0; k < meff; ++k) {
-      const V* s = (k == 0) ? src : c.basis_slot(k);
-      const R a = pick_r<R>(ss.coef_re[k], ss.coef_re_f[k]), b = pick_r<R>(ss.coef_im[k], ss.coef_im_f[k]);
-      V q[APT];
+    if (meff == 0)  // zero source: the result is zero
+      for (int ct = 0; ct < c.n_own; ++ct)
+        recomb_finalize<V, A, APT>(c, c.tile_base(ct), y, dst, extra, psi_other, nacc, gacc, ex0, ex1);
+    for (int i = 0; i < nch; ++i) {
+      const unsigned g = g0 + (unsigned)i;
+      const unsigned st = g % NS;
+      if (!mbar_wait_bounded(p, &ss.mbar[st], (g / NS) & 1u)) return false;
+      const int ct = i / meff, k = i - ct * meff;
+      const R a = (R)ss.coef_re_f[k], b = (R)ss.coef_im_f[k];
+      const V* buf = ring + (size_t)st * 4096;
 #pragma unroll
       for (int j = 0; j < APT; ++j) {
-        const int li = tid + j * kThreads;
-        q[j] = (li < T) ? ldv(s + base + li) : vzero<V>();
+        const V q = buf[tid + j * kThreads];
+        y[j].x += a * q.x - b * q.y;
+        y[j].y += a * q.y + b * q.x;
       }
+      if (k == meff - 1) {
+        recomb_finalize<V, A, APT>(c, c.tile_base(ct), y, dst, extra, psi_other, nacc, gacc, ex0, ex1);
 #pragma unroll
-      for (int j = 0; j < APT; ++j) {
-        y[j].x += a * q[j].x - b * q[j].y;
-        y[j].y += a * q[j].y + b * q[j].x;
+        for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
+      }
+      __syncthreads();  // every thread is done with stage st
+      if (tid == 0 && i + NS < nch) {
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&ss.mbar[st], kChunk);
+        tma_load_1d(ring + (size_t)st * 4096, chunk_src(i + NS), kChunk, &ss.mbar[st]);
       }
     }
+    c.ring_count = g0 + (unsigned)nch;
+  } else {
+    for (int ct = 0; ct < c.n_own; ++ct) {
+      const size_t base = c.tile_base(ct);
+      V y[APT];
 #pragma unroll
-    for (int j = 0; j < APT; ++j) {
-      const int li = tid + j * kThreads;
-      if (li >= T) continue;
-      const size_t gi = base + li;
-      const R yr = y[j].x, yi = y[j].y;
-      stv(dst + gi, y[j]);
-      nacc += (A)(yr * yr + yi * yi);
-      if (extra == kExtraOverlapTarget) {
-        const double2 f = reinterpret_cast<const double2*>(p.target)[gi];
-        ex0 += f.x * (double)yr + f.y * (double)yi;
-        ex1 += f.x * (double)yi - f.y * (double)yr;
-      } else if (extra == kExtraGradOverlap) {
-        V q;
-        if (p.hc_kind == KG_HC_SX_SITE) {
-          q = ldv(psi_other + (gi ^ ((size_t)1 << p.hc_site)));
-          const R h = pick_r<R>(0.5 * p.hc_amp, 0.5f * (float)p.hc_amp);
-          q.x *= h;
-          q.y *= h;
-        } else {
-          const unsigned mk = (unsigned)p.hc_mask;
-          const int nz = __popc(mk) - 2 * __popc((unsigned)gi & mk);
-          const R dz = pick_r<R>(p.hc_amp * 0.5 * (double)nz, (float)p.hc_amp * 0.5f * (float)nz);
-          q = ldv(psi_other + gi);
-          q.x *= dz;
-          q.y *= dz;
+      for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
+      int k = 0;
+      for (; k + 2 <= meff; k += 2) {  // two basis vectors in flight
+        V q[2][APT];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const V* s = (k + u == 0) ? src : c.basis_slot(k + u);
+#pragma unroll
+          for (int j = 0; j < APT; ++j) {
+            const int li = tid + j * kThreads;
+            q[u][j] = (li < T) ? ldv(s + base + li) : vzero<V>();
+          }
         }
-        gacc += (A)(yr * q.y - yi * q.x);  // Im(conj(y) q)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const R a = pick_r<R>(ss.coef_re[k + u], ss.coef_re_f[k + u]);
+          const R b = pick_r<R>(ss.coef_im[k + u], ss.coef_im_f[k + u]);
+#pragma unroll
+          for (int j = 0; j < APT; ++j) {
+            y[j].x += a * q[u][j].x - b * q[u][j].y;
+            y[j].y += a * q[u][j].y + b * q[u][j].x;
+          }
+        }
       }
+      for (; k < meff; ++k) {
+        const V* s = (k == 0) ? src : c.basis_slot(k);
+        const R a = pick_r<R>(ss.coef_re[k], ss.coef_re_f[k]), b = pick_r<R>(ss.coef_im[k], ss.coef_im_f[k]);
+        V q[APT];
+#pragma unroll
+        for (int j = 0; j < APT; ++j) {
+          const int li = tid + j * kThreads;
+          q[j] = (li < T) ? ldv(s + base + li) : vzero<V>();
+        }
+#pragma unroll
+        for (int j = 0; j < APT; ++j) {
+          y[j].x += a * q[j].x - b * q[j].y;
+          y[j].y += a * q[j].y + b * q[j].x;
+        }
+      }
+      recomb_finalize<V, A, APT>(c, base, y, dst, extra, psi_other, nacc, gacc, ex0, ex1);
     }
   }
   double out[3] = {0.0, 0.0, 0.0};
@@ -540,6 +712,7 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
   }
   nrm_dst = ss.nrm_out;
   e = make_double2(out[1], out[2]);
+  c.mark(5);
   return true;
 }
 
@@ -549,13 +722,72 @@ __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// Partner sums of the bonds that leave a 4096-amplitude tile (complex64, 512 threads x 8):
+// x[j] = sum_{b >= 11, antiparallel} (Jxy/2) src[partner] (+ (u/2) src[site flip] for an Sx
+// control on a site >= 12), for the thread's amplitudes li = tid + 512 j of the tile at base.
+__device__ __forceinline__ void cross_sums64(const EvalParams& p, size_t base, const float2* __restrict__ src,
+                                             float hxy, float cu_sx, float2 (&x)[8]) {
+  constexpr int APT = 8, NT = kThreads;
+  const int tid = threadIdx.x;
+  const int L1 = p.L - 1;
+#pragma unroll
+  for (int j = 0; j < APT; ++j) x[j] = f2(0.f);
+  if (L1 > 11) {  // bond 11: bit 11 = bit 2 of j, bit 12 = lowest tile bit
+    const int bt = (int)((base >> 12) & 1u);
+    const float2* q0 = src + (base ^ ((size_t)1 << 12)) + tid;
+#pragma unroll
+    for (int j = 0; j < APT; ++j)
+      if (((j >> 2) & 1) != bt) x[j] = f2fma(f2(hxy), ldv(q0 + (j ^ 4) * NT), x[j]);
+  }
+  // bonds between tile bits (the same for the whole tile): up to four bonds' loads in flight
+  unsigned act = 0;  // bit (b - 12) set: bond b antiparallel for this tile
+  for (int b = 12; b < L1; ++b)
+    if (((base >> b) ^ (base >> (b + 1))) & 1u) act |= 1u << (b - 12);
+  while (act) {
+    int bb[4];
+    float mm[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (act) {
+        bb[u] = 12 + __ffs(act) - 1;
+        act &= act - 1;
+        mm[u] = hxy;
+      } else {
+        bb[u] = bb[0];
+        mm[u] = 0.f;
+      }
+    }
+    float2 q[4][APT];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2* pu = src + (base ^ ((size_t)3 << bb[u])) + tid;
+#pragma unroll
+      for (int j = 0; j < APT; ++j) q[u][j] = (u == 0 || mm[u] != 0.f) ? ldv(pu + j * NT) : f2(0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(mm[u]), q[u][j], x[j]);
+  }
+  if (p.hc_kind == KG_HC_SX_SITE && p.hc_site >= 12) {
+    const float2* q0 = src + (base ^ ((size_t)1 << p.hc_site)) + tid;
+#pragma unroll
+    for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(cu_sx), ldv(q0 + j * NT), x[j]);
+  }
+}
+
 // Lanczos loop of one slice for complex64 tiles of 4096 amplitudes (512 threads x 8), every
-// CTA holding its (at most 2) tiles resident.  Same recurrence as lanczos_generic; the
+// CTA holding its (at most 2) tiles resident.  Same recurrence as lanczos_generic, except
+// that the basis slots hold the raw vectors W_k (slot 0: psi) rather than v_k: they are
+// written anyway for the other tiles' partners, and since v_k = (W_k - alpha v_{k-1}) / b_k
+// the recombination sum_k c_k v_k is a sum over the W_k with transformed coefficients.  The
 // amplitude of thread tid in register j is li = tid + 512 j, so
 //   bonds 0..7  (bits inside tid):  antiparallel test shared by all j, partner (tid ^ 3<<b) + 512 j
 //   bond 8      (bit 8 of tid, bit 0 of j): partner (tid ^ 256) + 512 (j ^ 1)
 //   bonds 9, 10 (bits of j):        partner in registers, test known at compile time
-//   bond 11 and up:                 other tiles (X recurrence, stage 1)
+//   bond 11 and up:                 other tiles (partner sums of W, X recurrence)
+// The partner sums of W_{k+1} are loaded right after the barrier of step k, so their latency
+// overlaps thread 0's FP64 work on alpha_k, b_{k+1}.
 __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, double nrm_src, double uj) {
   const EvalParams& p = *c.p;
   SmemSlice& ss = *c.ss;
@@ -571,81 +803,70 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
   const unsigned xt = (unsigned)(tid ^ (tid >> 1));
   const int t8 = (tid >> 8) & 1;
   const int n_own = c.n_own;
-  float2 W[NB][APT];
+  // shared memory: v_k of the own tiles (read by neighbours in the stencil), and two
+  // thread-private arrays: X_k and the partner sums of W_k (no synchronisation needed)
+  float2* sv = c.sv[0];
+  float2* sxs = c.sv[1];
+  float2* sx = c.sx;
+  float2 W[NB][APT];  // W_k of the own amplitudes (k = 0: psi); after stage 1: -b_k v_{k-1}
   double amax = 0.0, bmax = 0.0;  // thread 0: running maxima for the breakdown test
   if (tid == 0) lz_init(ss, nrm_src, m);
+#pragma unroll
+  for (int cc = 0; cc < NB; ++cc) {
+    if (cc >= n_own) break;
+    const size_t base = c.tile_base(cc);
+    float2 xs[APT];
+    cross_sums64(p, base, src, hxy, cu_sx, xs);
+#pragma unroll
+    for (int j = 0; j < APT; ++j) sxs[cc * T + tid + j * NT] = xs[j];
+  }
+#pragma unroll
+  for (int cc = 0; cc < NB; ++cc) {
+    if (cc >= n_own) break;
+    const size_t base = c.tile_base(cc);
+#pragma unroll
+    for (int j = 0; j < APT; ++j) W[cc][j] = ldv(src + base + tid + j * NT);
+  }
   __syncthreads();
   if (ss.meff == 0) return true;
   for (int k = 0; k < m; ++k) {
     const bool last = (k == m - 1);
-    const float2* wsrc = (k == 0) ? src : c.wbuf(k);
-    float2* wdst = last ? nullptr : c.wbuf(k + 1);
-    float2* vslot = (k == 0) ? nullptr : c.basis_slot(k);
+    float2* wdst = last ? nullptr : c.basis_slot(k + 1);  // W_{k+1}: basis slot k+1
     const float ap = ss.f_ap, ib = ss.f_ib, bk = ss.f_bk;
-    float2* s_cur = c.sv[k & 1];
-    const float2* s_prev = c.sv[(k & 1) ^ 1];
     float2 acc_a = f2(0.f), acc_n = f2(0.f), acc_q = f2(0.f);
-    // ---- stage 1: v_k of the own amplitudes; X_k from the partners in other tiles
+    // ---- stage 1: v_k = (W_k - alpha v_{k-1}) / b_k, X_k = (XS_k - alpha X_{k-1}) / b_k,
+    //      and W <- -b_k v_{k-1}, the first part of W_{k+1}
 #pragma unroll
     for (int cc = 0; cc < NB; ++cc) {
       if (cc >= n_own) break;
       const size_t base = c.tile_base(cc);
-      float2* sc = s_cur + cc * T;
-      const float2* sp = s_prev + cc * T;
-      float2* sx = c.sx + cc * T;
-      if (k == 0) {
-#pragma unroll
-        for (int j = 0; j < APT; ++j) W[cc][j] = ldv(src + base + tid + j * NT);
-      }
-      float2 x[APT];
 #pragma unroll
       for (int j = 0; j < APT; ++j) {
-        const int li = tid + j * NT;
-        float2 v;
+        const int li = cc * T + tid + j * NT;
+        const float2 xs = sxs[li];
+        float2 v, x;
         if (k == 0) {
           v = f2mul(W[cc][j], f2(ib));
-          x[j] = f2(0.f);
+          x = f2mul(xs, f2(ib));
+          W[cc][j] = f2(0.f);
         } else {
-          v = f2mul(f2fma(f2(-ap), sp[li], W[cc][j]), f2(ib));
-          stv(vslot + base + li, v);
-          x[j] = f2mul(f2(-ap), sx[li]);
+          const float2 vp = sv[li];
+          v = f2mul(f2fma(f2(-ap), vp, W[cc][j]), f2(ib));
+          x = f2mul(f2fma(f2(-ap), sx[li], xs), f2(ib));
+          W[cc][j] = f2mul(f2(-bk), vp);
         }
-        sc[li] = v;
+        sv[li] = v;
+        sx[li] = x;
       }
-      if (L1 > 11) {  // bond 11: bit 11 = bit 2 of j, bit 12 = lowest tile bit
-        const int bt = (int)((base >> 12) & 1u);
-        const float2* q0 = wsrc + (base ^ ((size_t)1 << 12)) + tid;
-#pragma unroll
-        for (int j = 0; j < APT; ++j)
-          if (((j >> 2) & 1) != bt) x[j] = f2fma(f2(hxy), ldv(q0 + (j ^ 4) * NT), x[j]);
-      }
-      for (int b = 12; b < L1; ++b) {  // bonds between tile bits: the same for the whole tile
-        if (((base >> b) ^ (base >> (b + 1))) & 1u) {
-          const float2* q0 = wsrc + (base ^ ((size_t)3 << b)) + tid;
-          float2 q[APT];
-#pragma unroll
-          for (int j = 0; j < APT; ++j) q[j] = ldv(q0 + j * NT);
-#pragma unroll
-          for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(hxy), q[j], x[j]);
-        }
-      }
-      if (hc_sx && hs >= 12) {
-        const float2* q0 = wsrc + (base ^ ((size_t)1 << hs)) + tid;
-#pragma unroll
-        for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(cu_sx), ldv(q0 + j * NT), x[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < APT; ++j) sx[tid + j * NT] = f2mul(x[j], f2(ib));
     }
     __syncthreads();
+    c.mark(0);
     // ---- stage 2: W_{k+1} = H v_k - b_k v_{k-1}; partial sums
 #pragma unroll
     for (int cc = 0; cc < NB; ++cc) {
       if (cc >= n_own) break;
       const size_t base = c.tile_base(cc);
-      const float2* sc = s_cur + cc * T;
-      const float2* sp = s_prev + cc * T;
-      const float2* sx = c.sx + cc * T;
+      const float2* sc = sv + cc * T;
       float2 h[APT];
 #pragma unroll
       for (int j = 0; j < APT; ++j) h[j] = f2(0.f);
@@ -678,9 +899,8 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
         const unsigned xg = (gi ^ (gi >> 1)) & c.maskL1;
         float d = qz * (float)(L1 - 2 * __popc(xg));
         if (!hc_sx) d += cu_sz * 0.5f * (float)(__popc(mk) - 2 * __popc(gi & mk));
-        float2 w = f2fma(f2(d), v[j], f2fma(f2(hxy), h[j], sx[li]));
+        float2 w = f2fma(f2(d), v[j], f2fma(f2(hxy), h[j], f2add(sx[cc * T + li], W[cc][j])));
         if (hc_sx && hs < 12) w = f2fma(f2(cu_sx), sc[li ^ (1 << hs)], w);
-        if (k > 0) w = f2fma(f2(-bk), sp[li], w);
         acc_a = f2fma(v[j], w, acc_a);
         acc_n = f2fma(w, w, acc_n);
         acc_q = f2fma(v[j], v[j], acc_q);
@@ -689,8 +909,30 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
       }
     }
     float acc[3] = {acc_a.x + acc_a.y, acc_n.x + acc_n.y, acc_q.x + acc_q.y};
+    c.mark(1);
     double out[3];
     if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
+    c.mark(2);
+    // partner sums of W_{k+1} (visible to every CTA after the barrier), then this thread's
+    // own W_{k+1} back from L2; both before the FP64 scalar work of thread 0, so that the
+    // loads overlap it (W is not held in registers across the partner loads)
+    if (!last) {
+#pragma unroll
+      for (int cc = 0; cc < NB; ++cc) {
+        if (cc >= n_own) break;
+        float2 xs[APT];
+        cross_sums64(p, c.tile_base(cc), wdst, hxy, cu_sx, xs);
+#pragma unroll
+        for (int j = 0; j < APT; ++j) sxs[cc * T + tid + j * NT] = xs[j];
+      }
+#pragma unroll
+      for (int cc = 0; cc < NB; ++cc) {
+        if (cc >= n_own) break;
+        const size_t base = c.tile_base(cc);
+#pragma unroll
+        for (int j = 0; j < APT; ++j) W[cc][j] = ldv(wdst + base + tid + j * NT);
+      }
+    }
     if (tid == 0) lz_after_reduce(ss, k, last, out);
     __syncthreads();
     const int code = ss.code1;
@@ -702,10 +944,9 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
       float n1[1] = {0.f};
       const float ra = ss.f_alpha;
       for (int cc = 0; cc < n_own; ++cc) {
-        const float2* sc = s_cur + cc * T;
 #pragma unroll
         for (int j = 0; j < APT; ++j) {
-          const float2 r = f2fma(f2(-ra), sc[tid + j * NT], W[cc][j]);
+          const float2 r = f2fma(f2(-ra), sv[cc * T + tid + j * NT], W[cc][j]);
           n1[0] += r.x * r.x + r.y * r.y;
         }
       }
@@ -715,6 +956,7 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
     }
     if (tid == 0) lz_finish_step(ss, k, last, p.bd_tol, amax, bmax);
     __syncthreads();
+    c.mark(3);
     if (ss.stop) break;
   }
   return true;
@@ -729,7 +971,7 @@ __device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_sr
   if constexpr (FAST) ok = lanczos_res64(c, src, nrm_src, uj);
   else ok = lanczos_generic<V, A, APT, TPC, RES>(c, src, nrm_src, uj);
   if (!ok) return false;
-  return finish_slice<V, A, APT>(c, src, nrm_src, tau, dst, extra, psi_other, nrm_dst, e);
+  return finish_slice<V, A, APT, FAST>(c, src, nrm_src, tau, dst, extra, psi_other, nrm_dst, e);
 }
 
 // chi_N = beta f, ||chi_N||, and G_N = 2 dt Im <chi_N|Hc|psi_N>.
@@ -831,15 +1073,29 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
   c.D = (size_t)1 << p.L;
   c.ntiles = (int)(c.D >> p.t_bits);
   c.n_own = (c.ntiles - c.g.rank + c.g.size - 1) / c.g.size;
+  c.paired = (c.ntiles >= 2 && 2 * c.g.size == c.ntiles);
+  c.alt = 0x55555555u & (unsigned)(c.ntiles - 1);
   c.maskL1 = (p.L >= 2) ? ((1u << (p.L - 1)) - 1u) : 0u;
   c.err_max = 0.0;
   c.breakdowns = 0;
+  c.ring_count = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&ss.mbar[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  c.prof_on = (p.prof != nullptr && blockIdx.x == 0);
+  c.prof_last = clock64();
+  const long long prof_t0 = c.prof_last;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) c.prof_acc[i] = 0;
   const bool lead = (blockIdx.x == 0 && threadIdx.x == 0);
 
   // ---- forward sweep (Alg. "Basic GRAPE", step 4)
   double nrm_prev;
   if (!init_state<V>(c, fwd_slot<V>(c, 0), nrm_prev)) return;
   if (lead) p.nrm[0] = nrm_prev;
+  c.mark(6);
   double2 beta = make_double2(0.0, 0.0);
   for (int j = 1; j <= p.N; ++j) {
     double nrm_new;
@@ -866,6 +1122,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
     double nchi, gim;
     if (!init_costate<V>(c, beta, chi[0], psiN, nchi, gim)) return;
     if (lead) p.G[p.N] = 2.0 * p.dt * gim;
+    c.mark(6);
     int cur = 0;
     const int C = p.ckpt;
     const int nseg = (C > 0) ? (p.N + C - 1) / C : 1;
@@ -915,6 +1172,11 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
     if (threadIdx.x == 0) {
       p.scal[kScErrMax] = em;
       p.scal[kScBreakdowns] = (double)c.breakdowns;
+      if (c.prof_on) {
+        c.mark(6);
+        for (int i = 0; i < 7; ++i) p.prof[i] = c.prof_acc[i];
+        p.prof[7] = clock64() - prof_t0;
+      }
     }
   }
 }

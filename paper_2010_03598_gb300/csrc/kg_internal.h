@@ -48,6 +48,7 @@ struct EvalParams {
   int* ctrl;                // [kCtrlStatus, kCtrlAbort]
   long long wait_limit_ns;
   int debug_fault;          // 1: CTA 0 skips its arrival at the first group barrier
+  long long* prof;          // [8] phase cycles of CTA 0, or null
 };
 
 }  // namespace kg
