@@ -171,6 +171,30 @@ kg_status kg_destroy(kg_handle* handle);
  * its next wait, and the launch ends; the context stays usable.  ns must be >= 1. */
 kg_status kg_set_wait_limit_ns(int64_t ns);
 
+/* Size of the library's fixed device scratch array used by kg_evaluate_static. */
+#define KG_STATIC_WORKSPACE_BYTES (64ull * 1024ull * 1024ull)
+
+/* One fidelity(+gradient) evaluation that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory themselves — a host
+ * application or runtime that owns the whole device memory budget and forbids further
+ * cudaMalloc after start-up, code without a device allocator at hand (plain C callers that
+ * have no torch or workspace allocator), or latency-critical loops that must not pay
+ * cudaMalloc's implicit device synchronisation.  Instead of a caller workspace it uses a
+ * fixed scratch array of KG_STATIC_WORKSPACE_BYTES (64 MiB) compiled into the library
+ * (a static __device__ array: every GPU that loads the library holds it until the process
+ * exits).  Arguments are those of kg_create + kg_evaluate (device pointers, caller-owned);
+ * KG_FLAG_HOST_STAGING is not accepted.  Requests whose workspace (kg_workspace_bytes) exceeds
+ * the array are rejected with KG_ERR_WORKSPACE before any device work.
+ * The call is synchronous: it enqueues on cuda_stream (NULL = legacy default stream), waits
+ * for it and returns the device status like kg_sync.  Every call on a device shares the one
+ * array, which keeps the last call's contents (the control block is cleared at each call):
+ * calls that overlap on the GPU — from several host threads or streams — race and give wrong
+ * results.  The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress, which may load the library's device code); make that first call
+ * outside any stream capture.  No device or host memory is allocated on the success path. */
+kg_status kg_evaluate_static(const kg_chain* chain, const kg_options* opts, const double* u, const void* psi0,
+                             const void* target, double* fid, double* grad, void* cuda_stream);
+
 /* Test hook for failure detection.  kind 1: in the next launch, CTA 0 does not arrive at
  * the first group barrier (a member that never joins); the other CTAs' waits, and its own,
  * run out after the wait limit and the launch ends with KG_ERR_TIMEOUT (read by kg_sync).

@@ -15,6 +15,7 @@ KG_GRAD_NONE, KG_GRAD_CENTERED, KG_GRAD_ZEROTH = 0, 1, 2
 KG_HC_SX_SITE, KG_HC_SZ_SITES = 0, 1
 KG_FLAG_HOST_STAGING = 1
 KG_FLAG_PHASE_TIMING = 2
+KG_STATIC_WORKSPACE_BYTES = 64 << 20
 
 
 class KgChain(ctypes.Structure):
@@ -53,6 +54,8 @@ SIGNATURES = {
     "kg_destroy": (ctypes.c_int, [_P]),
     "kg_set_wait_limit_ns": (ctypes.c_int, [ctypes.c_int64]),
     "kg_debug_set_fault": (ctypes.c_int, [ctypes.c_int32]),
+    "kg_evaluate_static": (ctypes.c_int, [ctypes.POINTER(KgChain), ctypes.POINTER(KgOptions), _P, _P, _P, _P, _P,
+                                          _P]),
 }
 
 _lib = None

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -344,3 +345,102 @@ kg_status kg_destroy(kg_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- evaluation without allocation
+// Scratch for kg_evaluate_static: a fixed device array in place of a caller workspace (see the
+// header for who needs this).  In host code the name g_static_ws is only a host-side handle of
+// the symbol, not a device address; the device address is resolved once per device below.
+static __device__ __align__(256) unsigned char g_static_ws[KG_STATIC_WORKSPACE_BYTES];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+void* g_static_addr[kStaticMaxDevices];  // device address of g_static_ws, per device (set-up once)
+std::mutex g_static_mu;                  // guards the set-up only; calls themselves must not overlap
+
+// Set-up, once per device, with that device current.
+kg_status static_scratch_address(int dev, void** out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return KG_OK;
+}
+
+}  // namespace
+
+extern "C" kg_status kg_evaluate_static(const kg_chain* chain, const kg_options* opts, const double* u,
+                                        const void* psi0, const void* target, double* fid, double* grad,
+                                        void* cuda_stream) {
+  kg_status st = check_args(chain, opts);
+  if (st != KG_OK) return st;
+  if (opts->flags & KG_FLAG_HOST_STAGING)
+    return fail(KG_ERR_INVALID_ARG, "kg_evaluate_static does not take KG_FLAG_HOST_STAGING");
+  const Layout lay = make_layout(chain, opts);
+  if (lay.total > KG_STATIC_WORKSPACE_BYTES)
+    return fail(KG_ERR_WORKSPACE, "kg_evaluate_static: the problem needs " + std::to_string(lay.total) +
+                                      " bytes of workspace; the static scratch holds " +
+                                      std::to_string(KG_STATIC_WORKSPACE_BYTES) +
+                                      " (use kg_create with a caller workspace)");
+  if (!u || !psi0 || !target || !fid) return fail(KG_ERR_INVALID_ARG, "u, psi0, target and fid must not be NULL");
+  if (opts->grad != KG_GRAD_NONE && !grad) return fail(KG_ERR_INVALID_ARG, "grad must not be NULL");
+  if (((uintptr_t)psi0 % 16) || ((uintptr_t)target % 16) || ((uintptr_t)u % 8) || ((uintptr_t)fid % 8) ||
+      (grad && ((uintptr_t)grad % 8)))
+    return fail(KG_ERR_INVALID_ARG, "psi0/target must be 16-byte aligned, u/fid/grad 8-byte aligned");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(KG_ERR_UNSUPPORTED, "device index above 63");
+  void* ws = nullptr;
+  st = static_scratch_address(dev, &ws);
+  if (st != KG_OK) return st;
+
+  // launch configuration: the same choice kg_create makes
+  const int t = default_tile_bits(chain, opts);
+  const int ntiles = 1 << (chain->L - t);
+  int variant = kg::kVariantStreaming;
+  int ctas = 0;
+  const int tpc = kg::resident_tiles_per_cta(opts->prec);
+  if (tpc > 0) {
+    int maxr = 0;
+    e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantResident, t, &maxr);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    int c = (opts->ctas > 0) ? opts->ctas : (ntiles >= 2 ? ntiles / 2 : 1);
+    if (c > ntiles) c = ntiles;
+    if (c > maxr) c = maxr;
+    if (c > kg::kMaxCtas) c = kg::kMaxCtas;
+    if (c >= 1 && (long long)c * tpc >= ntiles) {
+      variant = (t == kg::max_tile_bits(opts->prec)) ? kg::kVariantResidentFull : kg::kVariantResident;
+      ctas = c;
+    }
+  }
+  if (variant == kg::kVariantStreaming) {
+    int maxc = 0;
+    e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantStreaming, t, &maxc);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (maxc < 1) return fail(KG_ERR_UNSUPPORTED, "evaluation kernel does not fit on this device");
+    ctas = (opts->ctas > 0) ? opts->ctas : ntiles;
+    if (ctas > ntiles) ctas = ntiles;
+    if (ctas > maxc) ctas = maxc;
+    if (ctas > kg::kMaxCtas) ctas = kg::kMaxCtas;
+  }
+  kg_handle h;  // on the stack: nothing is allocated
+  h.chain = *chain;
+  h.opts = *opts;
+  if (!(h.opts.breakdown_tol > 0.0)) h.opts.breakdown_tol = (opts->prec == KG_PREC_C128) ? 1e-12 : 1e-5;
+  h.lay = lay;
+  h.ws = (char*)ws;
+  h.bytes = KG_STATIC_WORKSPACE_BYTES;
+  h.stream = (cudaStream_t)cuda_stream;
+  h.device = dev;
+  h.ctas = ctas;
+  h.t_bits = t;
+  h.variant = variant;
+  st = enqueue(&h, u, psi0, target, fid, grad);
+  if (st != KG_OK) return st;
+  return kg_sync(&h, nullptr);
+}
