@@ -171,6 +171,46 @@ kg_status kg_destroy(kg_handle* handle);
  * its next wait, and the launch ends; the context stays usable.  ns must be >= 1. */
 kg_status kg_set_wait_limit_ns(int64_t ns);
 
+/* ---------------------------------------------------------------- batched evaluation
+ * Many independent pulses (each its own chain, controls, initial state and target; shared
+ * kg_options) evaluated by ONE cooperative persistent launch: the host schedules every problem
+ * onto a group of CTAs (largest first, onto the least loaded CTAs); each group synchronises
+ * on its own barrier, so small problems run on single CTAs without any grid-wide wait.
+ * Complex64 path only (KG_PREC_C64_F64REC).  The launch is CUDA-graph capturable: all
+ * pointers are fixed when the batch is created. */
+typedef struct kg_batch kg_batch;  /* opaque host object; owns no device memory */
+
+typedef struct kg_batch_schedule {
+  int32_t ctas;           /* CTAs of the launch; 0 = every CTA that fits co-resident */
+  int32_t tiles_per_cta;  /* 1 or 2 (0 = 2): a problem of T tiles gets ceil(T/tiles_per_cta) CTAs */
+  int32_t reserved0;      /* must be 0 */
+  int32_t reserved1;      /* must be 0 */
+} kg_batch_schedule;
+
+/* Workspace bytes for B problems (independent of the schedule). */
+kg_status kg_batch_workspace_bytes(int32_t B, const kg_chain* chains, const kg_options* opts, size_t* bytes);
+
+/* Create a batch.  chains[B] (host), opts (host, shared), sched (host, nullable = defaults).
+ * u[B], psi0[B], target[B], grad[B]: HOST arrays of DEVICE pointers with the shapes of
+ * kg_evaluate (u[b] has opts->N doubles, psi0[b]/target[b] 2^L_b complex128); fid: device
+ * array of B doubles.  The pointers are copied; the buffers they point to must stay valid for
+ * every launch.  Uploads the problem table into the workspace (synchronously). */
+kg_status kg_batch_create(kg_batch** batch, int32_t B, const kg_chain* chains, const kg_options* opts,
+                          const kg_batch_schedule* sched, const double* const* u, const void* const* psi0,
+                          const void* const* target, double* fid, double* const* grad, void* workspace,
+                          size_t bytes, void* cuda_stream);
+
+/* Enqueue one evaluation of every problem of the batch on the batch's stream (a 64-byte
+ * memset of the control block plus one cooperative kernel; capturable in a CUDA graph). */
+kg_status kg_batch_launch(kg_batch* batch);
+
+/* Wait for the stream and return the device status (as kg_sync). ctas_used (nullable) receives
+ * the grid size of the launch. */
+kg_status kg_batch_sync(kg_batch* batch, int32_t* ctas_used);
+
+/* Destroy (host memory only). NULL is a no-op. */
+kg_status kg_batch_destroy(kg_batch* batch);
+
 /* Size of the library's fixed device scratch array used by kg_evaluate_static. */
 #define KG_STATIC_WORKSPACE_BYTES (64ull * 1024ull * 1024ull)
 

@@ -37,6 +37,11 @@ class KgReport(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 8)]
 
 
+class KgBatchSchedule(ctypes.Structure):
+    _fields_ = [("ctas", ctypes.c_int32), ("tiles_per_cta", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
 
@@ -54,6 +59,14 @@ SIGNATURES = {
     "kg_destroy": (ctypes.c_int, [_P]),
     "kg_set_wait_limit_ns": (ctypes.c_int, [ctypes.c_int64]),
     "kg_debug_set_fault": (ctypes.c_int, [ctypes.c_int32]),
+    "kg_batch_workspace_bytes": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(KgChain), ctypes.POINTER(KgOptions),
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "kg_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(KgChain),
+                                       ctypes.POINTER(KgOptions), ctypes.POINTER(KgBatchSchedule), _P, _P, _P, _P, _P,
+                                       _P, ctypes.c_size_t, _P]),
+    "kg_batch_launch": (ctypes.c_int, [_P]),
+    "kg_batch_sync": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "kg_batch_destroy": (ctypes.c_int, [_P]),
     "kg_evaluate_static": (ctypes.c_int, [ctypes.POINTER(KgChain), ctypes.POINTER(KgOptions), _P, _P, _P, _P, _P,
                                           _P]),
 }

@@ -187,3 +187,74 @@ class KGrapeFidelity(torch.autograd.Function):
 def fidelity(u: torch.Tensor, engine: KGrape, psi0: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
     """Differentiable F(u) (shape [1]) through the K-GRAPE adjoint kernels."""
     return KGrapeFidelity.apply(u, engine, psi0, target)
+
+
+class KGrapeBatch:
+    """Many independent pulses evaluated by one cooperative launch (complex64 path).
+
+    ``chains`` (one ChainSpec per problem) and shared ``opts``; ``u``, ``psi0``, ``target`` are
+    lists of device tensors (kept referenced).  ``fid`` (B) and ``grads`` (B x N) are device
+    outputs owned by this object.  ``launch()`` enqueues (capturable in a CUDA graph),
+    ``sync()`` waits and raises on a device error.
+    """
+
+    def __init__(self, chains, opts: Options, u, psi0, target, device=None, stream=None, ctas: int = 0,
+                 tiles_per_cta: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("KGrapeBatch needs a CUDA device; there is no CPU fallback")
+        B = len(chains)
+        if not (len(u) == len(psi0) == len(target) == B):
+            raise ValueError("one u, psi0 and target per chain")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.chains, self.opts, self.B = list(chains), opts, B
+        for i, (c, ut, pt, ft) in enumerate(zip(chains, u, psi0, target)):
+            D = 1 << c.L
+            if ut.dtype != torch.float64 or ut.numel() != opts.N or ut.device != self.device:
+                raise ValueError(f"problem {i}: u must be {opts.N} float64 on {self.device}")
+            for name, t in (("psi0", pt), ("target", ft)):
+                if t.dtype != torch.complex128 or t.numel() != D or t.device != self.device:
+                    raise ValueError(f"problem {i}: {name} must be {D} complex128 on {self.device}")
+        self._keep = (list(u), list(psi0), list(target))
+        carr = (_abi.KgChain * B)(*[c.to_c() for c in chains])
+        copts = opts.to_c()
+        n = ctypes.c_size_t(0)
+        check(lib().kg_batch_workspace_bytes(B, carr, ctypes.byref(copts), ctypes.byref(n)), "kg_batch_workspace_bytes")
+        self._ws_raw = torch.empty(n.value + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws_raw.data_ptr() + ((-self._ws_raw.data_ptr()) % 256)
+        self.fid = torch.zeros(B, dtype=torch.float64, device=self.device)
+        self.grads = torch.zeros(B, max(opts.N, 1), dtype=torch.float64, device=self.device)
+        P = ctypes.c_void_p * B
+        up = P(*[t.data_ptr() for t in u])
+        pp = P(*[t.data_ptr() for t in psi0])
+        fp = P(*[t.data_ptr() for t in target])
+        gp = P(*[self.grads[i].data_ptr() for i in range(B)])
+        sched = _abi.KgBatchSchedule(ctas, tiles_per_cta, 0, 0)
+        h = ctypes.c_void_p(0)
+        with torch.cuda.device(self.device):
+            check(lib().kg_batch_create(ctypes.byref(h), B, carr, ctypes.byref(copts), ctypes.byref(sched), up, pp,
+                                        fp, self.fid.data_ptr(), gp, ctypes.c_void_p(base), ctypes.c_size_t(n.value),
+                                        ctypes.c_void_p(self.stream.cuda_stream)), "kg_batch_create")
+        self._h = h
+        self.workspace_bytes = int(n.value)
+
+    def launch(self) -> None:
+        check(lib().kg_batch_launch(self._h), "kg_batch_launch")
+
+    def sync(self) -> int:
+        c = ctypes.c_int32(0)
+        with torch.cuda.device(self.device):
+            check(lib().kg_batch_sync(self._h, ctypes.byref(c)), "kg_batch_sync")
+        return int(c.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().kg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -2,9 +2,11 @@
 // launch configuration, and the synchronous host-buffer entry point.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <mutex>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -252,6 +254,7 @@ static kg_status enqueue(kg_handle* h, const double* u, const void* psi0, const 
   p.scal = (double*)(ws + h->lay.scal);
   p.bar = (unsigned long long*)(ws + h->lay.bar);
   p.red = (double*)(ws + h->lay.red);
+  p.red_stride = kg::kMaxCtas;
   p.ctrl = (int*)(ws + h->lay.ctrl);
   p.wait_limit_ns = g_wait_limit_ns.load();
   p.debug_fault = g_debug_fault.exchange(0);
@@ -444,3 +447,246 @@ extern "C" kg_status kg_evaluate_static(const kg_chain* chain, const kg_options*
   if (st != KG_OK) return st;
   return kg_sync(&h, nullptr);
 }
+
+// ---------------------------------------------------------------- batched evaluation
+struct kg_batch {
+  int B = 0;
+  kg_options opts{};
+  char* ws = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int ctas = 0;
+  size_t clear_off = 0, clear_bytes = 0;  // control block + barrier counters, zeroed per launch
+  kg::BatchParams bp{};
+};
+
+namespace {
+
+struct BatchLayout {
+  size_t ctrl = 0, bars = 0, reds = 0, probs = 0, item_off = 0, items = 0, total = 0;
+  std::vector<size_t> prob;  // start of each problem's own workspace
+  size_t max_items = 0;
+};
+
+int batch_tile_bits(const kg_chain& ch) { return ch.L < 12 ? ch.L : 12; }
+
+BatchLayout make_batch_layout(int B, const kg_chain* chains, const kg_options* o) {
+  BatchLayout l;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  l.ctrl = take(64 + sizeof(unsigned long long) * (size_t)B);  // ctrl words, then barrier counters
+  l.bars = l.ctrl + 64;
+  l.reds = take(sizeof(double) * kg::kBatchRedPerGroup * (size_t)B);
+  l.probs = take(sizeof(kg::EvalParams) * (size_t)B);
+  l.item_off = take(sizeof(int) * (size_t)(kg::kMaxCtas + 1));
+  for (int b = 0; b < B; ++b) l.max_items += (size_t)1 << (chains[b].L - batch_tile_bits(chains[b]));
+  l.items = take(sizeof(kg::BatchItem) * l.max_items);
+  l.prob.resize(B);
+  for (int b = 0; b < B; ++b) l.prob[b] = take(make_layout(&chains[b], o).total);
+  l.total = off;
+  return l;
+}
+
+kg_status check_batch(int B, const kg_chain* chains, const kg_options* o) {
+  if (B < 1) return fail(KG_ERR_INVALID_ARG, "batch size must be >= 1");
+  if (!chains || !o) return fail(KG_ERR_INVALID_ARG, "chains and options must not be NULL");
+  if (o->prec != KG_PREC_C64_F64REC) return fail(KG_ERR_UNSUPPORTED, "batched evaluation runs the complex64 path only");
+  if (o->flags != 0) return fail(KG_ERR_INVALID_ARG, "batched evaluation takes no flags");
+  if (o->tile_bits != 0 || o->ctas != 0)
+    return fail(KG_ERR_INVALID_ARG, "tile_bits and ctas are set by the batch schedule, not the options");
+  for (int b = 0; b < B; ++b) {
+    kg_status st = check_args(&chains[b], o);
+    if (st != KG_OK) return fail(st, "problem " + std::to_string(b) + ": " + g_last_error);
+  }
+  return KG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kg_status kg_batch_workspace_bytes(int32_t B, const kg_chain* chains, const kg_options* opts, size_t* bytes) {
+  kg_status st = check_batch(B, chains, opts);
+  if (st != KG_OK) return st;
+  if (!bytes) return fail(KG_ERR_INVALID_ARG, "bytes must not be NULL");
+  *bytes = make_batch_layout(B, chains, opts).total;
+  return KG_OK;
+}
+
+kg_status kg_batch_create(kg_batch** batch, int32_t B, const kg_chain* chains, const kg_options* opts,
+                          const kg_batch_schedule* sched, const double* const* u, const void* const* psi0,
+                          const void* const* target, double* fid, double* const* grad, void* workspace,
+                          size_t bytes, void* cuda_stream) {
+  if (!batch) return fail(KG_ERR_INVALID_ARG, "batch must not be NULL");
+  *batch = nullptr;
+  kg_status st = check_batch(B, chains, opts);
+  if (st != KG_OK) return st;
+  if (!u || !psi0 || !target || !fid || (opts->grad != KG_GRAD_NONE && !grad))
+    return fail(KG_ERR_INVALID_ARG, "u, psi0, target, fid (and grad) must not be NULL");
+  kg_batch_schedule sc{0, 0, 0, 0};
+  if (sched) sc = *sched;
+  if (sc.reserved0 || sc.reserved1) return fail(KG_ERR_INVALID_ARG, "schedule reserved fields must be 0");
+  if (sc.tiles_per_cta == 0) sc.tiles_per_cta = 2;
+  if (sc.tiles_per_cta != 1 && sc.tiles_per_cta != 2) return fail(KG_ERR_INVALID_ARG, "tiles_per_cta must be 1 or 2");
+  if (sc.ctas < 0 || sc.ctas > kg::kMaxCtas) return fail(KG_ERR_INVALID_ARG, "ctas must be 0..2048");
+  const BatchLayout lay = make_batch_layout(B, chains, opts);
+  if (!workspace || ((uintptr_t)workspace % kg::kAlign)) return fail(KG_ERR_WORKSPACE, "workspace NULL or not 256-byte aligned");
+  if (bytes < lay.total)
+    return fail(KG_ERR_WORKSPACE, "workspace too small: need " + std::to_string(lay.total) + " bytes");
+  for (int b = 0; b < B; ++b) {
+    if (!u[b] || !psi0[b] || !target[b] || (opts->grad != KG_GRAD_NONE && !grad[b]))
+      return fail(KG_ERR_INVALID_ARG, "problem " + std::to_string(b) + ": NULL input or output pointer");
+    if (((uintptr_t)psi0[b] % 16) || ((uintptr_t)target[b] % 16) || ((uintptr_t)u[b] % 8))
+      return fail(KG_ERR_INVALID_ARG, "problem " + std::to_string(b) + ": misaligned pointer");
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  int maxc = 0;
+  e = kg::batch_kernel_max_ctas(&maxc);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  int ctas = sc.ctas > 0 ? std::min(sc.ctas, maxc) : maxc;
+  if (ctas < 1) return fail(KG_ERR_UNSUPPORTED, "batch kernel does not fit on this device");
+
+  // ---- schedule: largest problems first, each onto the least loaded CTAs it needs
+  struct Job {
+    int b, g;
+    double cost;
+  };
+  std::vector<Job> jobs(B);
+  const double steps_per_slice = (double)opts->m;
+  for (int b = 0; b < B; ++b) {
+    const int t = batch_tile_bits(chains[b]);
+    const int ntiles = 1 << (chains[b].L - t);
+    int g = (ntiles + sc.tiles_per_cta - 1) / sc.tiles_per_cta;
+    g = std::min(g, std::min(kg::kBatchMaxGroup, ctas));
+    const double slices = (double)opts->N * (opts->grad != KG_GRAD_NONE ? 2.0 : 1.0) *
+                          (opts->ckpt_every > 0 ? 1.5 : 1.0);
+    const double amps_per_cta = (double)((size_t)1 << chains[b].L) / g;
+    const double step_us = (g > 1 ? 4.5 : 1.5) + 2.5 * amps_per_cta / 4096.0;
+    jobs[b] = {b, g, slices * steps_per_slice * step_us};
+  }
+  std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& c) { return a.cost > c.cost; });
+  std::vector<double> busy(ctas, 0.0);
+  std::vector<std::vector<kg::BatchItem>> lists(ctas);
+  std::vector<int> order(ctas);
+  for (const Job& jb : jobs) {
+    for (int i = 0; i < ctas; ++i) order[i] = i;
+    std::partial_sort(order.begin(), order.begin() + jb.g, order.end(),
+                      [&](int a, int c) { return busy[a] < busy[c] || (busy[a] == busy[c] && a < c); });
+    double start = 0.0;
+    for (int r = 0; r < jb.g; ++r) start = std::max(start, busy[order[r]]);
+    for (int r = 0; r < jb.g; ++r) {
+      busy[order[r]] = start + jb.cost;
+      lists[order[r]].push_back(kg::BatchItem{jb.b, r, jb.g, jb.b});
+    }
+  }
+  std::vector<int> item_off(ctas + 1, 0);
+  std::vector<kg::BatchItem> items;
+  for (int c = 0; c < ctas; ++c) {
+    item_off[c] = (int)items.size();
+    items.insert(items.end(), lists[c].begin(), lists[c].end());
+  }
+  item_off[ctas] = (int)items.size();
+
+  // ---- problem table
+  char* ws = (char*)workspace;
+  std::vector<kg::EvalParams> probs(B);
+  for (int b = 0; b < B; ++b) {
+    const kg_chain& ch = chains[b];
+    const Layout pl = make_layout(&ch, opts);
+    char* w = ws + lay.prob[b];
+    kg::EvalParams& p = probs[b];
+    p = kg::EvalParams{};
+    p.L = ch.L;
+    p.N = opts->N;
+    p.m = opts->m;
+    p.t_bits = batch_tile_bits(ch);
+    p.grad_mode = opts->grad;
+    p.hc_kind = ch.hc_kind;
+    p.hc_site = ch.hc_site;
+    p.ckpt = opts->ckpt_every;
+    p.hc_mask = ch.hc_site_mask;
+    p.Jxy = ch.Jxy;
+    p.Jz = ch.Jz;
+    p.hc_amp = ch.hc_amp;
+    p.dt = opts->dt;
+    p.bd_tol = (opts->breakdown_tol > 0.0) ? opts->breakdown_tol : 1e-5;
+    p.u = u[b];
+    p.psi0 = (const double*)psi0[b];
+    p.target = (const double*)target[b];
+    p.fid = fid + b;
+    p.grad = (opts->grad != KG_GRAD_NONE) ? grad[b] : nullptr;
+    p.basis = w + pl.basis;
+    p.traj = w + pl.traj;
+    p.seg = w + pl.seg;
+    p.chi = w + pl.chi;
+    p.wbuf = w + pl.wbuf;
+    p.xbuf = w + pl.xbuf;
+    p.G = (double*)(w + pl.G);
+    p.nrm = (double*)(w + pl.nrm);
+    p.scal = (double*)(w + pl.scal);
+    p.wait_limit_ns = g_wait_limit_ns.load();
+    p.debug_fault = 0;
+    p.prof = nullptr;
+  }
+  if ((e = cudaMemcpy(ws + lay.probs, probs.data(), sizeof(kg::EvalParams) * B, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(ws + lay.item_off, item_off.data(), sizeof(int) * (ctas + 1), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(ws + lay.items, items.data(), sizeof(kg::BatchItem) * items.size(), cudaMemcpyHostToDevice)))
+    return cuda_fail(e, "cudaMemcpy(batch tables)");
+
+  kg_batch* h = new kg_batch();
+  h->B = B;
+  h->opts = *opts;
+  h->ws = ws;
+  h->bytes = bytes;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->device = dev;
+  h->ctas = ctas;
+  h->clear_off = lay.ctrl;
+  h->clear_bytes = 64 + sizeof(unsigned long long) * (size_t)B;
+  h->bp.probs = (const kg::EvalParams*)(ws + lay.probs);
+  h->bp.item_off = (const int*)(ws + lay.item_off);
+  h->bp.items = (const kg::BatchItem*)(ws + lay.items);
+  h->bp.bars = (unsigned long long*)(ws + lay.bars);
+  h->bp.reds = (double*)(ws + lay.reds);
+  h->bp.ctrl = (int*)(ws + lay.ctrl);
+  *batch = h;
+  return KG_OK;
+}
+
+kg_status kg_batch_launch(kg_batch* b) {
+  if (!b) return fail(KG_ERR_INVALID_ARG, "batch must not be NULL");
+  cudaError_t e = cudaMemsetAsync(b->ws + b->clear_off, 0, b->clear_bytes, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch control block)");
+  e = kg::launch_batch_kernel(b->bp, b->ctas, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the batch kernel");
+  return KG_OK;
+}
+
+kg_status kg_batch_sync(kg_batch* b, int32_t* ctas_used) {
+  if (!b) return fail(KG_ERR_INVALID_ARG, "batch must not be NULL");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int ctrl[2] = {0, 0};
+  e = cudaMemcpy(ctrl, b->ws + b->clear_off, sizeof(ctrl), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+  if (ctas_used) *ctas_used = b->ctas;
+  const int st = ctrl[kg::kCtrlStatus];
+  if (st == KG_ERR_TIMEOUT) return fail(KG_ERR_TIMEOUT, "a device-side wait ran past its time limit");
+  if (st == KG_ERR_NONFINITE) return fail(KG_ERR_NONFINITE, "non-finite Lanczos coefficient or norm");
+  if (st != 0) return fail(KG_ERR_CUDA, "device status " + std::to_string(st));
+  return KG_OK;
+}
+
+kg_status kg_batch_destroy(kg_batch* b) {
+  delete b;
+  return KG_OK;
+}
+
+}  // extern "C"

@@ -96,12 +96,13 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem
 struct Group {
   int rank, size;
   unsigned long long* bar;   // monotone arrival counter (reset to 0 before each launch)
-  double* red;               // [2][kMaxCtas][kNRed] partial slots, alternating by reduction
+  double* red;               // [2][stride][kNRed] partial slots, alternating by reduction
   int* ctrl;                 // status word, abort flag
   long long wait_limit_ns;
   int phase;                 // reduction counter (slot parity)
   int skip_arrival;          // fault injection: do not arrive at the next barrier (then cleared)
   unsigned long long epoch;  // barriers passed so far (identical in every CTA of the group)
+  int stride;                // reduction slots per parity (>= size)
 };
 
 struct SmemRed {
@@ -198,7 +199,7 @@ __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, A (&vals)[NV
     for (int v = 0; v < NV; ++v) sm.warp_part[warp * kNRed + v] = (double)vals[v];
   }
   __syncthreads();
-  double* slots = g.red + (size_t)(g.phase & 1) * kMaxCtas * kNRed;
+  double* slots = g.red + (size_t)(g.phase & 1) * g.stride * kNRed;
   g.phase++;
   if (warp < NV) {
     double s = (lane < nw) ? sm.warp_part[lane * kNRed + warp] : 0.0;
@@ -237,7 +238,7 @@ __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, float (&vals
     for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
   }
   __syncthreads();
-  float2* slots = reinterpret_cast<float2*>(g.red + (size_t)(g.phase & 1) * kMaxCtas * kNRed);
+  float2* slots = reinterpret_cast<float2*>(g.red + (size_t)(g.phase & 1) * g.stride * kNRed);
   g.phase++;
   if (warp < NV) {
     FF s{(lane < nw) ? sm.warp_part_f[lane * kNRed + warp] : 0.f, 0.f};

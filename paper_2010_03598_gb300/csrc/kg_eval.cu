@@ -1048,21 +1048,23 @@ __device__ __forceinline__ V* fwd_slot(const Ctx<V>& c, int j) {
   return (V*)p.seg + (size_t)(C - 1 + (j & 1)) * c.D;
 }
 
+// One whole evaluation (forward sweep, overlap, co-state sweep, gradient) of problem p by the
+// group of `size` CTAs in which this CTA has rank `rank`.  Returns false if the group aborted.
 template <class V, class A, int APT, int TPC, bool RES, bool FAST>
-__global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_constant__ EvalParams p) {
-  extern __shared__ __align__(16) unsigned char smem_dyn[];
-  __shared__ SmemSlice ss;
+__device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, SmemSlice& ss,
+                                      unsigned char* smem_dyn, unsigned& ring_count) {
   Ctx<V> c;
   c.p = &p;
-  c.g.rank = blockIdx.x;
-  c.g.size = gridDim.x;
+  c.g.rank = rank;
+  c.g.size = size;
   c.g.bar = p.bar;
   c.g.red = p.red;
   c.g.ctrl = p.ctrl;
   c.g.wait_limit_ns = p.wait_limit_ns;
   c.g.phase = 0;
   c.g.epoch = 0;
-  c.g.skip_arrival = (p.debug_fault == 1 && blockIdx.x == 0) ? 1 : 0;
+  c.g.skip_arrival = (p.debug_fault == 1 && rank == 0) ? 1 : 0;
+  c.g.stride = p.red_stride;
   c.ss = &ss;
   c.t = p.t_bits;
   c.tile = 1 << p.t_bits;
@@ -1078,22 +1080,17 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
   c.maskL1 = (p.L >= 2) ? ((1u << (p.L - 1)) - 1u) : 0u;
   c.err_max = 0.0;
   c.breakdowns = 0;
-  c.ring_count = 0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&ss.mbar[i], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  c.prof_on = (p.prof != nullptr && blockIdx.x == 0);
+  c.ring_count = ring_count;
+  c.prof_on = (p.prof != nullptr && rank == 0);
   c.prof_last = clock64();
   const long long prof_t0 = c.prof_last;
 #pragma unroll
   for (int i = 0; i < 8; ++i) c.prof_acc[i] = 0;
-  const bool lead = (blockIdx.x == 0 && threadIdx.x == 0);
+  const bool lead = (rank == 0 && threadIdx.x == 0);
 
   // ---- forward sweep (Alg. "Basic GRAPE", step 4)
   double nrm_prev;
-  if (!init_state<V>(c, fwd_slot<V>(c, 0), nrm_prev)) return;
+  if (!init_state<V>(c, fwd_slot<V>(c, 0), nrm_prev)) return false;
   if (lead) p.nrm[0] = nrm_prev;
   c.mark(6);
   double2 beta = make_double2(0.0, 0.0);
@@ -1103,7 +1100,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
     const int extra = (j == p.N) ? kExtraOverlapTarget : kExtraNone;
     if (!krylov_slice<V, A, APT, TPC, RES, FAST>(c, fwd_slot<V>(c, j - 1), nrm_prev, p.u[j - 1], p.dt, fwd_slot<V>(c, j),
                                            extra, nullptr, nrm_new, e))
-      return;
+      return false;
     if (lead) p.nrm[j] = nrm_new;
     nrm_prev = nrm_new;
     if (j == p.N) beta = e;
@@ -1120,7 +1117,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
     V* chi[2] = {(V*)p.chi, (V*)p.chi + c.D};
     const V* psiN = fwd_slot<V>(c, p.N);
     double nchi, gim;
-    if (!init_costate<V>(c, beta, chi[0], psiN, nchi, gim)) return;
+    if (!init_costate<V>(c, beta, chi[0], psiN, nchi, gim)) return false;
     if (lead) p.G[p.N] = 2.0 * p.dt * gim;
     c.mark(6);
     int cur = 0;
@@ -1138,7 +1135,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
           double nn;
           double2 e;
           if (!krylov_slice<V, A, APT, TPC, RES, FAST>(c, prev, np, p.u[i - 1], p.dt, d, kExtraNone, nullptr, nn, e))
-            return;
+            return false;
           prev = d;
           np = nn;
         }
@@ -1152,15 +1149,15 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
         double2 e;
         if (!krylov_slice<V, A, APT, TPC, RES, FAST>(c, chi[cur], nchi, p.u[j - 1], -p.dt, chi[cur ^ 1],
                                                kExtraGradOverlap, psi_jm1, nn, e))
-          return;
+          return false;
         if (lead) p.G[j - 1] = 2.0 * p.dt * e.x;
         cur ^= 1;
         nchi = nn;
       }
     }
   }
-  // ---- outputs (CTA 0)
-  if (blockIdx.x == 0) {
+  // ---- outputs (rank 0)
+  if (rank == 0) {
     __syncthreads();
     if (p.grad_mode != KG_GRAD_NONE) {
       for (int j = threadIdx.x; j < p.N; j += blockDim.x) {
@@ -1179,6 +1176,88 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
       }
     }
   }
+  ring_count = c.ring_count;
+  return true;
+}
+
+template <class V, class A, int APT, int TPC, bool RES, bool FAST>
+__global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_constant__ EvalParams p) {
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  __shared__ SmemSlice ss;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&ss.mbar[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned ring_count = 0;
+  run_eval<V, A, APT, TPC, RES, FAST>(p, blockIdx.x, gridDim.x, ss, smem_dyn, ring_count);
+}
+
+// Many independent problems (complex64) in one cooperative launch.  Every CTA walks its own
+// list of items in the order the host scheduled them; a group of CTAs forms for one problem
+// and uses its own barrier counter.  Lists are ordered consistently (a global sequence), so a
+// CTA waiting in a group only waits for members that will reach that item.
+__global__ void __launch_bounds__(kThreads, 1) kg_batch_kernel(const __grid_constant__ BatchParams bp) {
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  __shared__ SmemSlice ss;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&ss.mbar[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned ring_count = 0;
+  const int i0 = bp.item_off[blockIdx.x], i1 = bp.item_off[blockIdx.x + 1];
+  for (int it = i0; it < i1; ++it) {
+    const BatchItem item = bp.items[it];
+    EvalParams p = bp.probs[item.problem];
+    p.bar = bp.bars + item.group;
+    p.red = bp.reds + (size_t)item.group * kBatchRedPerGroup;
+    p.red_stride = kBatchMaxGroup;
+    p.ctrl = bp.ctrl;
+    const int ntiles = 1 << (p.L - p.t_bits);
+    bool ok;
+    if (ntiles <= 2 * item.size && p.t_bits == 12)
+      ok = run_eval<float2, float, 8, 2, true, true>(p, item.rank, item.size, ss, smem_dyn, ring_count);
+    else if (ntiles <= 2 * item.size)
+      ok = run_eval<float2, float, 8, 2, true, false>(p, item.rank, item.size, ss, smem_dyn, ring_count);
+    else
+      ok = run_eval<float2, float, 8, 1, false, false>(p, item.rank, item.size, ss, smem_dyn, ring_count);
+    if (!ok) return;
+    __syncthreads();
+  }
+}
+
+size_t batch_smem_bytes() { return (size_t)3 * 2 * 4096 * sizeof(float2); }
+
+cudaError_t launch_batch_kernel(const BatchParams& bp, int ctas, cudaStream_t stream) {
+  const size_t smem = batch_smem_bytes();
+  cudaError_t err = cudaFuncSetAttribute(kg_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kg_batch_kernel, bp);
+}
+
+cudaError_t batch_kernel_max_ctas(int* out) {
+  const size_t smem = batch_smem_bytes();
+  cudaError_t err = cudaFuncSetAttribute(kg_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kg_batch_kernel, kThreads, smem);
+  if (err != cudaSuccess) return err;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *out = per_sm * sms;
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- host-side launch helpers

@@ -44,11 +44,31 @@ struct EvalParams {
   double* nrm;              // [N+1] ||psi_j|| of the forward sweep
   double* scal;             // [kScCount]
   unsigned long long* bar;  // group barrier counter
-  double* red;              // [2][kMaxCtas][kNRed] reduction slots
+  double* red;              // [2][red_stride][kNRed] reduction slots
+  int red_stride;           // slots per parity (>= CTAs of the group)
   int* ctrl;                // [kCtrlStatus, kCtrlAbort]
   long long wait_limit_ns;
   int debug_fault;          // 1: CTA 0 skips its arrival at the first group barrier
   long long* prof;          // [8] phase cycles of CTA 0, or null
+};
+
+// Batched launch: CTA c runs items [item_off[c], item_off[c+1]) in order; item i evaluates
+// problem `problem` as rank `rank` of a group of `size` CTAs with barrier counter bars[group]
+// and reduction slots reds + group * kBatchRedPerGroup.
+constexpr int kBatchMaxGroup = 64;
+constexpr size_t kBatchRedPerGroup = (size_t)2 * kBatchMaxGroup * kNRed;
+
+struct BatchItem {
+  int problem, rank, size, group;
+};
+
+struct BatchParams {
+  const EvalParams* probs;  // [B]
+  const int* item_off;      // [ctas + 1]
+  const BatchItem* items;
+  unsigned long long* bars;  // [groups]
+  double* reds;              // [groups][kBatchRedPerGroup]
+  int* ctrl;                 // shared status word and abort flag
 };
 
 }  // namespace kg

@@ -21,4 +21,8 @@ cudaError_t eval_kernel_max_ctas(int prec, int variant, int t_bits, int* out);
 int max_tile_bits(int prec);
 int resident_tiles_per_cta(int prec);
 
+// Batched evaluation kernel (complex64): cooperative launch (CUDA-graph capturable).
+cudaError_t launch_batch_kernel(const BatchParams& bp, int ctas, cudaStream_t stream);
+cudaError_t batch_kernel_max_ctas(int* out);
+
 }  // namespace kg

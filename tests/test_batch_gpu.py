@@ -1,0 +1,145 @@
+"""Batched persistent launch: many independent pulses in one cooperative kernel.
+
+Checked against the oracle (complex128) at the complex64 tolerances, against the
+single-problem path, across schedules (results must not depend on how problems are laid
+out on CTAs), and when the launch is captured in a CUDA graph.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2010_03598_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TF, TG = 1e-5, 1e-4
+
+
+def api():
+    from paper_2010_03598_gb300 import api as A
+    return A
+
+
+def make_problems(Ls, deltas, N, seed):
+    rng = np.random.default_rng(seed)
+    dev = torch.device("cuda", 0)
+    out = []
+    for L, d in zip(Ls, deltas):
+        u = rng.uniform(-1, 1, N)
+        f = W.draw_target(rng, 1 << L)
+        psi0 = W.neel_state(L)
+        out.append(dict(L=L, delta=d, u=u, psi0=psi0, target=f,
+                        ut=torch.tensor(u, device=dev), pt=torch.tensor(psi0, device=dev),
+                        ft=torch.tensor(f, device=dev)))
+    return out
+
+
+def run_batch(probs, opts, **sched):
+    A = api()
+    chains = [A.ChainSpec(p["L"], 1.0, p["delta"]) for p in probs]
+    b = A.KGrapeBatch(chains, opts, [p["ut"] for p in probs], [p["pt"] for p in probs], [p["ft"] for p in probs],
+                      **sched)
+    b.launch()
+    b.sync()
+    F = b.fid.cpu().numpy().copy()
+    G = b.grads.cpu().numpy()[:, : opts.N].copy()
+    b.close()
+    return F, G
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def nrel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def test_small_batch_vs_oracle():
+    # single-CTA problems (one tile, two tiles), the specialised full-tile path and a group of 2
+    Ls = [3, 5, 8, 10, 12, 13, 14]
+    deltas = [0.3, 1.1, 0.5, 1.7, 0.9, 0.2, 1.3]
+    N, m, dt = 6, 10, 0.05
+    probs = make_problems(Ls, deltas, N, 11)
+    F, G = run_batch(probs, api().Options(N, dt, m, prec="c64"))
+    for i, p in enumerate(probs):
+        ch = oracle.Chain(p["L"], 1.0, p["delta"])
+        Fr, gr, _ = oracle.evaluate(ch, p["u"], dt, m, p["psi0"], p["target"], "centered")
+        assert rel(F[i], Fr) <= TF, (p["L"], F[i], Fr)
+        assert nrel(G[i], gr) <= TG, (p["L"], nrel(G[i], gr))
+
+
+def test_batch_matches_single_problem_path_for_every_schedule():
+    A = api()
+    Ls = [10, 12, 13, 14, 15, 16, 11, 14]
+    deltas = [0.4, 1.0, 1.9, 0.1, 0.7, 1.2, 0.5, 1.6]
+    N, m, dt = 8, 12, 0.05
+    probs = make_problems(Ls, deltas, N, 12)
+    opts = A.Options(N, dt, m, prec="c64")
+    ref = []
+    for p in probs:
+        eng = A.KGrape(A.ChainSpec(p["L"], 1.0, p["delta"]), opts)
+        fid, grad = eng.evaluate(p["ut"], p["pt"], p["ft"])
+        eng.sync()
+        ref.append((float(fid.item()), grad.cpu().numpy().copy()))
+        eng.close()
+    for sched in (dict(), dict(tiles_per_cta=1), dict(ctas=16), dict(ctas=5, tiles_per_cta=1)):
+        F, G = run_batch(probs, opts, **sched)
+        for i in range(len(probs)):
+            assert rel(F[i], ref[i][0]) <= TF, (sched, i)
+            assert nrel(G[i], ref[i][1]) <= TG, (sched, i)
+
+
+def test_batch_launch_in_a_cuda_graph():
+    A = api()
+    probs = make_problems([9, 12, 14], [0.5, 1.0, 1.5], 5, 13)
+    opts = A.Options(5, 0.05, 10, prec="c64")
+    F0, G0 = run_batch(probs, opts)
+    s = torch.cuda.Stream()
+    chains = [A.ChainSpec(p["L"], 1.0, p["delta"]) for p in probs]
+    b = A.KGrapeBatch(chains, opts, [p["ut"] for p in probs], [p["pt"] for p in probs], [p["ft"] for p in probs],
+                      stream=s)
+    b.launch()
+    b.sync()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.launch()
+    for _ in range(2):
+        b.fid.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        F = b.fid.cpu().numpy()
+        G = b.grads.cpu().numpy()[:, :5]
+        assert np.array_equal(F, F0) and np.array_equal(G, G0)
+    b.close()
+
+
+def test_batch256_workload_against_single_runs_and_oracle():
+    A = api()
+    inst = W.batch_instances()
+    N, dt, m = W.BATCH_N, W.BATCH_DT, W.BATCH_M
+    dev = torch.device("cuda", 0)
+    for d in inst:
+        d["ut"] = torch.tensor(d["u"], device=dev)
+        d["pt"] = torch.tensor(d["psi0"], device=dev)
+        d["ft"] = torch.tensor(d["target"], device=dev)
+    opts = A.Options(N, dt, m, prec="c64")
+    F, G = run_batch(inst, opts)
+    assert np.all(np.isfinite(F)) and np.all((F > 0) & (F < 1))
+    # sampled pulses against the single-problem path
+    rng = np.random.default_rng(4)
+    for i in sorted(rng.choice(len(inst), 6, replace=False)):
+        d = inst[i]
+        eng = A.KGrape(A.ChainSpec(d["L"], 1.0, d["delta"]), opts)
+        fid, grad = eng.evaluate(d["ut"], d["pt"], d["ft"])
+        eng.sync()
+        assert rel(F[i], float(fid.item())) <= TF
+        assert nrel(G[i], grad.cpu().numpy()) <= TG
+        eng.close()
+    # the two smallest chains against the oracle
+    small = sorted(range(len(inst)), key=lambda i: (inst[i]["L"], i))[:2]
+    for i in small:
+        d = inst[i]
+        Fr, gr, _ = oracle.evaluate(oracle.Chain(d["L"], 1.0, d["delta"]), d["u"], dt, m, d["psi0"], d["target"])
+        assert rel(F[i], Fr) <= TF, (i, F[i], Fr)
+        assert nrel(G[i], gr) <= TG, (i, nrel(G[i], gr))
