@@ -224,6 +224,7 @@ def run_reference(args):
 
 def config_block(w, name, prec):
     return {"workload": name, "L": w.L, "D": w.D, "N": w.N, "m": w.m, "dt": w.dt, "delta": w.delta, "J": w.J,
+            "ckpt_every": w.ckpt,
             "hc": "Sx on site 1", "psi0": "Neel", "target": "seeded Gaussian, normalised", "prec": prec,
             "l2": "flushed between timed steps (512 MiB write); per-step working set > L2",
             "parallelism": "replicas (one independent evaluation per GPU)"}
@@ -267,8 +268,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def timed(prec, steps, warmup):
-        eng = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec=prec, tile_bits=args.tile_bits, ctas=args.ctas),
-                       device=dev)
+        eng = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec=prec, tile_bits=args.tile_bits, ctas=args.ctas,
+                                        ckpt_every=w.ckpt), device=dev)
         for _ in range(warmup):
             eng.evaluate(ut, pt, ft)
         rep = eng.sync()
@@ -308,7 +309,7 @@ def run_ours(args):
     ms_per_step = total_s * 1e3 / args.steps
     hbm, peak_kind = measured_peaks()
     per_launch_s = statistics.mean(ms) / 1e3
-    ab = alg_bytes(w, args.prec)
+    ab = alg_bytes(w, args.prec, w.ckpt)
     achieved = ab / per_launch_s / 1e9
     kernel_key = f"kg_eval_kernel<{'float2' if args.prec == 'c64' else 'double2'}>@{args.workload}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -321,7 +322,7 @@ def run_ours(args):
     if args.fp64_steps > 0 and args.prec != "c128":
         ms64, rep64, fid64, _ = timed("c128", args.fp64_steps, 1)
         t64 = max_over_ranks(sum(ms64) / 1e3)
-        a64 = alg_bytes(w, "c128") / (statistics.mean(ms64) / 1e3) / 1e9
+        a64 = alg_bytes(w, "c128", w.ckpt) / (statistics.mean(ms64) / 1e3) / 1e9
         fp64 = {"value": args.fp64_steps * world / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.fp64_steps,
                 "steps": args.fp64_steps, "hbm_gbs_algorithmic": a64, "hbm_frac": a64 / hbm,
                 "speedup_of_headline": value / (args.fp64_steps * world / t64),
@@ -343,7 +344,7 @@ def run_ours(args):
 def run_e2e(A, chain, w, args, dev, u, psi0, f, barrier, max_over_ranks, world):
     import torch
     eng = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec=args.prec, host_staging=True, tile_bits=args.tile_bits,
-                                    ctas=args.ctas), device=dev)
+                                    ctas=args.ctas, ckpt_every=w.ckpt), device=dev)
     uh = torch.tensor(u).pin_memory()
     ph = torch.tensor(psi0).pin_memory()
     fh = torch.tensor(f).pin_memory()

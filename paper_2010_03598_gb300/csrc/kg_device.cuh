@@ -149,7 +149,9 @@ __device__ __forceinline__ bool group_barrier(Group& g, SmemRed& sm) {
   if (threadIdx.x == 0) {
     int ok = 1;
     if (g.size > 1) {
-      __threadfence();
+      // The arrival is a release reduction: it orders this CTA's earlier writes (those of other
+      // threads through the bar.sync above) before the count; the acquire load below orders
+      // the group's writes before everything this CTA reads after the barrier.
       if (g.skip_arrival) {  // injected fault: this CTA never joins; its own wait runs out too
         g.skip_arrival = 0;
       } else {
@@ -160,8 +162,8 @@ __device__ __forceinline__ bool group_barrier(Group& g, SmemRed& sm) {
       unsigned long long t0 = 0;
       unsigned polls = 0;
       while (ld_acquire_u64(g.bar) < goal) {
-        if (ld_volatile_i32(g.ctrl + kCtrlAbort)) { ok = 0; break; }
-        if (++polls > 256) {
+        if ((++polls & 31u) == 0u) {
+          if (ld_volatile_i32(g.ctrl + kCtrlAbort)) { ok = 0; break; }
           const unsigned long long now = globaltimer_ns();
           if (t0 == 0) {
             t0 = now;
@@ -171,10 +173,9 @@ __device__ __forceinline__ bool group_barrier(Group& g, SmemRed& sm) {
             ok = 0;
             break;
           }
-          __nanosleep(32);
+          if (polls > 4096u) __nanosleep(64);
         }
       }
-      __threadfence();
     } else if (ld_volatile_i32(g.ctrl + kCtrlAbort)) {
       ok = 0;
     }

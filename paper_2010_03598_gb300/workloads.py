@@ -38,6 +38,7 @@ class Workload:
     delta: float
     J: float = 1.0
     seed: int = SEED_BASE
+    ckpt: int = 0  # keep every ckpt-th psi_j and recompute the rest in the backward sweep (0: keep all)
 
     @property
     def D(self) -> int:
@@ -59,7 +60,7 @@ WORKLOADS = {
     "xxz_L16_N200_m20": Workload("xxz_L16_N200_m20", L=16, N=200, dt=0.05, m=20, delta=1.0, seed=SEED_BASE + 2),
     "xxz_L20_N400_m20": Workload("xxz_L20_N400_m20", L=20, N=400, dt=0.05, m=20, delta=0.5, seed=SEED_BASE + 3),
     "xxz_L24_N400_m24_ckpt20": Workload("xxz_L24_N400_m24_ckpt20", L=24, N=400, dt=0.05, m=24, delta=0.5,
-                                        seed=SEED_BASE + 5),
+                                        seed=SEED_BASE + 5, ckpt=20),
 }
 
 # Batched workload: 256 pulses, L_i ~ U{10..16}, Delta_i ~ U(0, 2), N=200, dt=0.05, m=16.

@@ -274,3 +274,64 @@ def test_member_that_never_arrives_times_out_cleanly():
     eng.evaluate(ut, pt, ft)
     assert eng.sync()["status"] == 0
     eng.close()
+
+
+# ------------------------------------------------------------------ adjoint vs finite differences
+def test_L20_adjoint_gradient_vs_central_finite_differences():
+    # Central FD of F (FP64 path, step 1e-4) at 16 seeded slice indices.  The centred gradient
+    # is an approximation with error O(dt^3) per component (App. B): measured 1.9e-4 relative at
+    # dt = 0.05; the zeroth-order gradient, O(dt^2), is 50x further off, so 1e-3 discriminates.
+    # The complex64 autograd gradient must match the FP64 path's gradient (1e-4).
+    w = W.WORKLOADS["xxz_L20_N400_m20"]
+    u, psi0, f = W.instance(w)
+    idx = W.fd_indices(w)
+    A = api()
+    chain = A.ChainSpec(w.L, w.Jxy, w.Jz)
+    ut, pt, ft = to_dev(u, psi0, f)
+    e128 = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec="c128"))
+    e128.evaluate(ut, pt, ft)
+    e128.sync()
+    g128 = e128.grad[: w.N].cpu().numpy().copy()
+    h = 1e-4
+    fd = []
+    for j in idx:
+        vals = []
+        for s in (1.0, -1.0):
+            uu = u.copy()
+            uu[j] += s * h
+            ut.copy_(torch.tensor(uu))
+            e128.evaluate(ut, pt, ft)
+            e128.sync()
+            vals.append(float(e128.fid.item()))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    e128.close()
+    assert nrel(g128[idx], fd) <= 1e-3, nrel(g128[idx], fd)
+    # complex64 adjoint through torch.autograd
+    ut.copy_(torch.tensor(u))
+    e64 = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec="c64"))
+    ut.requires_grad_(True)
+    F = A.fidelity(ut, e64, pt, ft)
+    F.sum().backward()
+    g64 = ut.grad.cpu().numpy()
+    assert nrel(g64, g128) <= 1e-4
+    assert nrel(g64[idx], fd) <= 1e-3
+    e64.close()
+
+
+# ------------------------------------------------------------------ L=24 with checkpoints
+def test_L24_checkpointed_backward_sweep():
+    # psi_j kept every 20 slices and recomputed in the backward sweep: bitwise equal to keeping
+    # every psi_j; complex64 against complex128 on a short pulse at the full chain size.
+    w = W.WORKLOADS["xxz_L24_N400_m24_ckpt20"]
+    A = api()
+    chain = A.ChainSpec(w.L, w.Jxy, w.Jz)
+    u, psi0, f = W.instance(w, N=12)
+    F0, g0, rep0 = run_gpu(chain, A.Options(12, w.dt, w.m, prec="c64", ckpt_every=0), u, psi0, f)
+    F1, g1, rep1 = run_gpu(chain, A.Options(12, w.dt, w.m, prec="c64", ckpt_every=5), u, psi0, f)
+    assert F0 == F1 and np.array_equal(g0, g1)
+    assert abs(rep1["norm_final"] - 1.0) < 1e-5
+    u2, psi02, f2 = W.instance(w, N=2)
+    F64, g64, _ = run_gpu(chain, A.Options(2, w.dt, w.m, prec="c64", ckpt_every=1), u2, psi02, f2)
+    F128, g128, _ = run_gpu(chain, A.Options(2, w.dt, w.m, prec="c128", ckpt_every=1), u2, psi02, f2)
+    check("c64", F64, g64, F128, g128)
