@@ -35,6 +35,8 @@ enum ExtraKind { kExtraNone = 0, kExtraOverlapTarget = 1, kExtraGradOverlap = 2 
 constexpr int kLogNT = 9;  // log2(kThreads)
 static_assert((1 << kLogNT) == kThreads, "kLogNT must match kThreads");
 
+constexpr int kRingStages = 6;  // 6 x 32 KB: all of the resident path's shared memory
+
 struct SmemSlice {
   SmemRed red;
   double alpha[kMaxM];
@@ -50,7 +52,7 @@ struct SmemSlice {
   double s_ap, s_ib, s_bk, s_alpha, s_b2, beta_m, nrm_out, s_ib0;
   float f_ap, f_ib, f_bk, f_alpha, f_ib0, f_bk0, f_beta_m;
   int code1, stop, meff, broke;
-  unsigned long long mbar[4];  // bulk-copy ring of the recombination (resident complex64 path)
+  unsigned long long mbar[kRingStages];  // bulk-copy ring of the recombination (resident complex64 path)
 };
 
 template <class R> __device__ __forceinline__ R pick_r(double d, float f);
@@ -528,6 +530,27 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
   const int tid = threadIdx.x;
   const int T = c.tile;
   const int meff = ss.meff;
+  // Complex64 resident path: the recombination streams the own tiles of the basis through a
+  // ring of kRingStages 32 KB bulk copies in the shared memory the Lanczos loop no longer
+  // needs; the first copies do not depend on c, so they are issued before the exponential.
+  constexpr int NS = kRingStages;
+  constexpr uint32_t kChunk = 4096u * 8u;  // one tile of one complex64 basis vector
+  auto chunk_src = [&](int i) -> const V* {
+    const int ct = i / meff, k = i - (i / meff) * meff;
+    return ((k == 0) ? src : c.basis_slot(k)) + c.tile_base(ct);
+  };
+  if constexpr (WBASIS) {
+    fence_proxy_async();  // earlier generic-proxy writes (basis, psi, ring area) before bulk copies
+    __syncthreads();
+    if (tid == 0) {
+      const int nch = c.n_own * meff;
+      for (int i = 0; i < nch && i < NS; ++i) {
+        const unsigned st = (c.ring_count + (unsigned)i) % NS;
+        mbar_arrive_expect_tx(&ss.mbar[st], kChunk);
+        tma_load_1d(c.sv[0] + (size_t)st * 4096, chunk_src(i), kChunk, &ss.mbar[st]);
+      }
+    }
+  }
   // ---- small exponential and recombination coefficients (warp 0, FP64)
   if (tid < 32) {
     const bool broke = ss.broke != 0;
@@ -593,24 +616,9 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
     // Complex64 resident path: stream the own tiles of the basis through a 4-stage ring of
     // 32 KB bulk copies (TMA) in the now idle shared memory; one chunk = one tile of one
     // basis vector.  Thread 0 issues, every thread waits on the chunk's barrier phase.
-    constexpr int NS = 4;
-    constexpr uint32_t kChunk = 4096u * (uint32_t)sizeof(float2);
     V* ring = c.sv[0];
     const int nch = c.n_own * meff;
     const unsigned g0 = c.ring_count;
-    fence_proxy_async();  // earlier generic-proxy writes (basis, psi, ring area) before bulk copies
-    __syncthreads();
-    auto chunk_src = [&](int i) -> const V* {
-      const int ct = i / meff, k = i - (i / meff) * meff;
-      return ((k == 0) ? src : c.basis_slot(k)) + c.tile_base(ct);
-    };
-    if (tid == 0) {
-      for (int i = 0; i < nch && i < NS; ++i) {
-        const unsigned st = (g0 + (unsigned)i) % NS;
-        mbar_arrive_expect_tx(&ss.mbar[st], kChunk);
-        tma_load_1d(ring + (size_t)st * 4096, chunk_src(i), kChunk, &ss.mbar[st]);
-      }
-    }
     V y[APT];
 #pragma unroll
     for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
@@ -1185,7 +1193,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&ss.mbar[i], 1);
+    for (int i = 0; i < kRingStages; ++i) mbar_init(&ss.mbar[i], 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -1201,7 +1209,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_batch_kernel(const __grid_cons
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&ss.mbar[i], 1);
+    for (int i = 0; i < kRingStages; ++i) mbar_init(&ss.mbar[i], 1);
     fence_mbar_init();
   }
   __syncthreads();
