@@ -89,6 +89,56 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem
                : "memory");
 }
 
+// ---------------------------------------------------------------- tensor memory (TMEM)
+// The complex64 resident path keeps thread-private arrays (the tile-leaving part X of H v_k
+// and the own W_k) in tensor memory instead of shared memory: a warp may access the 32 TMEM
+// lanes of its quarter of the warpgroup (lanes 32 (warp % 4) ...) and, with the 32x32b
+// shape, thread t of the warp reads or writes row 32 (warp % 4) + t.  Allocation is done by
+// one whole warp, which writes the TMEM address to shared memory; the same warp frees it.
+__device__ __forceinline__ void tmem_alloc(uint32_t* smem_dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(smem_dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// 8 complex64 values (16 columns) of this thread's TMEM row; load and wait in one statement,
+// so the registers are never used before the data has arrived.
+__device__ __forceinline__ void tmem_ld8c(uint32_t taddr, float2 (&v)[8]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+}
+__device__ __forceinline__ void tmem_st8c(uint32_t taddr, const float2 (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};\n"
+      "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
+      "r"(__float_as_uint(v[0].x)), "r"(__float_as_uint(v[0].y)), "r"(__float_as_uint(v[1].x)),
+      "r"(__float_as_uint(v[1].y)), "r"(__float_as_uint(v[2].x)), "r"(__float_as_uint(v[2].y)),
+      "r"(__float_as_uint(v[3].x)), "r"(__float_as_uint(v[3].y)), "r"(__float_as_uint(v[4].x)),
+      "r"(__float_as_uint(v[4].y)), "r"(__float_as_uint(v[5].x)), "r"(__float_as_uint(v[5].y)),
+      "r"(__float_as_uint(v[6].x)), "r"(__float_as_uint(v[6].y)), "r"(__float_as_uint(v[7].x)),
+      "r"(__float_as_uint(v[7].y))
+      : "memory");
+}
+
 // ---------------------------------------------------------------- group context
 // A group is the set of CTAs that cooperate on one problem.  All CTAs of a group are
 // co-resident (cooperative launch), execute the same sequence of barriers/reductions,
@@ -109,6 +159,7 @@ struct SmemRed {
   double warp_part[32 * kNRed];
   float warp_part_f[32 * kNRed];
   double out[kNRed];
+  float2 cta_ff[kNRed];  // this CTA's float-float partials (single-CTA groups)
   int flag;
 };
 
@@ -138,6 +189,17 @@ __device__ __forceinline__ FF ff_warp_sum(FF a) {
     a = ff_add(a, FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
   return a;
 }
+
+// Product of two float-float values (TwoProduct of the high parts with an FMA, plus the
+// cross terms); about 44 significant bits, the accuracy of the operands.
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  const float t = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  const float hi = __fadd_rn(p, t);
+  return {hi, __fsub_rn(t, __fsub_rn(hi, p))};
+}
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
 
 // Barrier with a time limit.  Returns false (for every thread of the CTA) if the group
 // aborted or this CTA's wait ran past the limit; in the latter case it records
@@ -267,6 +329,57 @@ __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, float (&vals
 #pragma unroll
   for (int v = 0; v < NV; ++v) out[v] = sm.out[v];
   return true;
+}
+
+// The same float-float reduction split in two, so that the caller can act between the
+// barrier and the sum (complex64 resident path): reduce_ff_arrive forms this CTA's partials
+// and passes the group barrier (false: the group aborted); reduce_ff_collect, executed by
+// warp 0 alone, sums the partials in rank order and leaves the totals in every lane.
+template <int NV>
+__device__ __forceinline__ bool reduce_ff_arrive(Group& g, SmemRed& sm, float (&vals)[NV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
+  }
+  __syncthreads();
+  float2* slots = reinterpret_cast<float2*>(g.red + (size_t)(g.phase & 1) * g.stride * kNRed);
+  g.phase++;  // every thread: reduce_ff_collect reads the slots of parity (phase - 1)
+  if (warp < NV) {
+    FF s{(lane < nw) ? sm.warp_part_f[lane * kNRed + warp] : 0.f, 0.f};
+    s = ff_warp_sum(s);
+    if (lane == 0) {
+      if (g.size > 1) __stcg(slots + (size_t)g.rank * kNRed + warp, make_float2(s.hi, s.lo));
+      else sm.cta_ff[warp] = make_float2(s.hi, s.lo);
+    }
+  }
+  if (g.size > 1) return group_barrier(g, sm);
+  __syncthreads();
+  return ld_volatile_i32(g.ctrl + kCtrlAbort) == 0;
+}
+template <int NV>
+__device__ __forceinline__ void reduce_ff_collect(Group& g, SmemRed& sm, FF (&out)[NV]) {
+  const int lane = threadIdx.x & 31;
+  const float2* slots = reinterpret_cast<const float2*>(g.red + (size_t)((g.phase - 1) & 1) * g.stride * kNRed);
+  if (g.size == 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = FF{sm.cta_ff[v].x, sm.cta_ff[v].y};
+    return;
+  }
+  FF s[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) s[v] = FF{0.f, 0.f};
+  for (int r = lane; r < g.size; r += 32) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float2 q = __ldcg(slots + (size_t)r * kNRed + v);
+      s[v] = ff_add(s[v], FF{q.x, q.y});
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = ff_warp_sum(s[v]);
 }
 
 // ---------------------------------------------------------------- small exponential

@@ -19,10 +19,10 @@
 // CTA forms c = exp(-i sigma dt T) e_1 (one warp, FP64) and recombines
 // psi' = ||psi|| sum_k c_k v_k for its own tiles (App. A).
 //
-// Resident variant (RES): every CTA owns at most TPC tiles; W and X of its amplitudes stay in
-// registers and v_k, v_{k-1} of its tiles in shared memory for the whole slice.  Streaming
-// variant: one tile at a time, W from the global W buffer, X from a global scratch vector,
-// v_{k-1} from the basis.
+// Resident variant (RES): every CTA owns at most TPC tiles; W and X of its amplitudes stay on
+// chip (registers and shared memory; tensor memory in the complex64 full-tile loop) and v_k,
+// v_{k-1} of its tiles in shared memory for the whole slice.  Streaming variant: one tile at
+// a time, W from the global W buffer, X from a global scratch vector, v_{k-1} from the basis.
 #include <cuda_runtime.h>
 
 #include "kg_device.cuh"
@@ -36,6 +36,9 @@ constexpr int kLogNT = 9;  // log2(kThreads)
 static_assert((1 << kLogNT) == kThreads, "kLogNT must match kThreads");
 
 constexpr int kRingStages = 6;  // 6 x 32 KB: all of the resident path's shared memory
+constexpr int kLzStages = 4;    // Lanczos partner ring: 4 x 32 KB behind the 64 KB of v_k
+constexpr int kLzMaxChunks = 2 * (1 + (kMaxL - 13) + 1);  // two tiles: bond 11, outer bonds, Sx site
+constexpr uint32_t kTmemCols = 256;  // X and W of two tiles: 64 columns per warp, 4 warps per lane quarter
 
 struct SmemSlice {
   SmemRed red;
@@ -53,6 +56,14 @@ struct SmemSlice {
   float f_ap, f_ib, f_bk, f_alpha, f_ib0, f_bk0, f_beta_m;
   int code1, stop, meff, broke;
   unsigned long long mbar[kRingStages];  // bulk-copy ring of the recombination (resident complex64 path)
+  // resident complex64 path: the Lanczos step's ring of partner-tile copies, its chunk table,
+  // the float-float sums of every step (for the FP64 tridiagonal), the TMEM address
+  unsigned long long lmbar[kLzStages];
+  unsigned ctab[kLzMaxChunks];
+  int ct_start[3];
+  float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
+  unsigned ff_e_set;
+  uint32_t tmem_base;
 };
 
 template <class R> __device__ __forceinline__ R pick_r(double d, float f);
@@ -167,7 +178,9 @@ struct Ctx {
   unsigned maskL1;  // bonds 0..L-2 in (i ^ i>>1)
   double err_max;
   int breakdowns;
-  unsigned ring_count;   // bulk-copy chunks consumed so far (ring stage and phase parity)
+  unsigned ring_count;   // recombination bulk copies consumed so far (ring stage and phase parity)
+  unsigned lz_count;     // Lanczos partner bulk copies consumed so far (complex64 resident path)
+  uint32_t tm;           // this warp's TMEM address: its lane quarter, its 64-column group
   bool prof_on;          // phase timing (CTA 0, thread 0)
   long long prof_last;
   long long prof_acc[8];
@@ -628,22 +641,24 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
     for (int i = 0; i < nch; ++i) {
       const unsigned g = g0 + (unsigned)i;
       const unsigned st = g % NS;
-      if (!mbar_wait_bounded(p, &ss.mbar[st], (g / NS) & 1u)) return false;
+      const bool ok = mbar_wait_bounded(p, &ss.mbar[st], (g / NS) & 1u);
       const int ct = i / meff, k = i - ct * meff;
-      const R a = (R)ss.coef_re_f[k], b = (R)ss.coef_im_f[k];
-      const V* buf = ring + (size_t)st * 4096;
+      if (ok) {
+        const R a = (R)ss.coef_re_f[k], b = (R)ss.coef_im_f[k];
+        const V* buf = ring + (size_t)st * 4096;
 #pragma unroll
-      for (int j = 0; j < APT; ++j) {
-        const V q = buf[tid + j * kThreads];
-        y[j].x += a * q.x - b * q.y;
-        y[j].y += a * q.y + b * q.x;
-      }
-      if (k == meff - 1) {
-        recomb_finalize<V, A, APT>(c, c.tile_base(ct), y, dst, extra, psi_other, nacc, gacc, ex0, ex1);
+        for (int j = 0; j < APT; ++j) {
+          const V q = buf[tid + j * kThreads];
+          y[j].x += a * q.x - b * q.y;
+          y[j].y += a * q.y + b * q.x;
+        }
+        if (k == meff - 1) {
+          recomb_finalize<V, A, APT>(c, c.tile_base(ct), y, dst, extra, psi_other, nacc, gacc, ex0, ex1);
 #pragma unroll
-        for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
+          for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
+        }
       }
-      __syncthreads();  // every thread is done with stage st
+      if (__syncthreads_or(!ok)) return false;  // every thread is done with stage st
       if (tid == 0 && i + NS < nch) {
         fence_proxy_async();
         mbar_arrive_expect_tx(&ss.mbar[st], kChunk);
@@ -730,58 +745,120 @@ __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Partner sums of the bonds that leave a 4096-amplitude tile (complex64, 512 threads x 8):
-// x[j] = sum_{b >= 11, antiparallel} (Jxy/2) src[partner] (+ (u/2) src[site flip] for an Sx
-// control on a site >= 12), for the thread's amplitudes li = tid + 512 j of the tile at base.
-__device__ __forceinline__ void cross_sums64(const EvalParams& p, size_t base, const float2* __restrict__ src,
-                                             float hxy, float cu_sx, float2 (&x)[8]) {
-  constexpr int APT = 8, NT = kThreads;
-  const int tid = threadIdx.x;
+// Chunk table of the complex64 resident path.  The partner amplitudes of the bonds that
+// leave a 4096-amplitude tile come from other tiles as whole contiguous blocks:
+//   bond 11 (bit 11 = the top in-tile bit, bit 12 = the lowest tile bit): the own half
+//     h = 1 - bt (bt = bit 12 of the tile) pairs with half bt of tile base ^ 2^12, element
+//     for element;
+//   bond b >= 12, antiparallel for the whole tile: tile base ^ (3 << b), element for element;
+//   an Sx control on site s >= 12: tile base ^ (1 << s), element for element.
+// Entry: bits 3.. = source offset in units of 2048 amplitudes (16 KB), bit 2 = whole tile
+// (32 KB, feeds every own amplitude) rather than one half, bit 1 = the own half h fed by a
+// half block, bit 0 = weight of the Sx control instead of Jxy/2.  Tile 0's entries come
+// first, then tile 1's: the ring fetches tile 1's blocks while tile 0 is being computed.
+__device__ __forceinline__ void build_chunk_table(const Ctx<float2>& c) {
+  const EvalParams& p = *c.p;
+  SmemSlice& ss = *c.ss;
   const int L1 = p.L - 1;
-#pragma unroll
-  for (int j = 0; j < APT; ++j) x[j] = f2(0.f);
-  if (L1 > 11) {  // bond 11: bit 11 = bit 2 of j, bit 12 = lowest tile bit
-    const int bt = (int)((base >> 12) & 1u);
-    const float2* q0 = src + (base ^ ((size_t)1 << 12)) + tid;
-#pragma unroll
-    for (int j = 0; j < APT; ++j)
-      if (((j >> 2) & 1) != bt) x[j] = f2fma(f2(hxy), ldv(q0 + (j ^ 4) * NT), x[j]);
-  }
-  // bonds between tile bits (the same for the whole tile): up to four bonds' loads in flight
-  unsigned act = 0;  // bit (b - 12) set: bond b antiparallel for this tile
-  for (int b = 12; b < L1; ++b)
-    if (((base >> b) ^ (base >> (b + 1))) & 1u) act |= 1u << (b - 12);
-  while (act) {
-    int bb[4];
-    float mm[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (act) {
-        bb[u] = 12 + __ffs(act) - 1;
-        act &= act - 1;
-        mm[u] = hxy;
-      } else {
-        bb[u] = bb[0];
-        mm[u] = 0.f;
+  int n = 0;
+  ss.ct_start[0] = 0;
+  for (int cc = 0; cc < 2; ++cc) {
+    if (cc < c.n_own) {
+      const size_t base = c.tile_base(cc);
+      if (L1 > 11) {
+        const unsigned bt = (unsigned)((base >> 12) & 1u);
+        const size_t off = ((base ^ ((size_t)1 << 12)) >> 11) + bt;
+        ss.ctab[n++] = ((unsigned)off << 3) | ((1u - bt) << 1);
       }
+      for (int b = 12; b < L1; ++b)
+        if (((base >> b) ^ (base >> (b + 1))) & 1u)
+          ss.ctab[n++] = ((unsigned)((base ^ ((size_t)3 << b)) >> 11) << 3) | 4u;
+      if (p.hc_kind == KG_HC_SX_SITE && p.hc_site >= 12)
+        ss.ctab[n++] = ((unsigned)((base ^ ((size_t)1 << p.hc_site)) >> 11) << 3) | 5u;
     }
-    float2 q[4][APT];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float2* pu = src + (base ^ ((size_t)3 << bb[u])) + tid;
-#pragma unroll
-      for (int j = 0; j < APT; ++j) q[u][j] = (u == 0 || mm[u] != 0.f) ? ldv(pu + j * NT) : f2(0.f);
+    ss.ct_start[cc + 1] = n;
+  }
+}
+
+// Thread 0: bulk copy of chunk i of the table from vector `vec` into ring stage g % stages
+// (g = the chunk's running number), completing on that stage's barrier.
+__device__ __forceinline__ void lz_issue(const Ctx<float2>& c, const float2* vec, int i, unsigned g) {
+  SmemSlice& ss = *c.ss;
+  const unsigned e = ss.ctab[i];
+  const unsigned st = g % kLzStages;
+  const uint32_t bytes = (e & 4u) ? 32768u : 16384u;
+  mbar_arrive_expect_tx(&ss.lmbar[st], bytes);
+  tma_load_1d(c.sv[1] + (size_t)st * 4096, vec + ((size_t)(e >> 3) << 11), bytes, &ss.lmbar[st]);
+}
+
+// Thread 0, complex64 resident path: alpha_k and b_{k+1}^2 = ||W||^2 + alpha^2 (||v||^2 - 2)
+// from the float-float sums o = (<v|W>, ||W||^2, ||v||^2) of step k (about 44 bits; the FP64
+// tridiagonal is formed from the same sums once the slice's steps are done).  code1 as in
+// lz_after_reduce.
+__device__ __forceinline__ FF lzf_after_reduce(SmemSlice& ss, int k, bool last, const FF (&o)[3]) {
+  ss.ff_a[k] = make_float2(o[0].hi, o[0].lo);
+  ss.ff_n[k] = make_float2(o[1].hi, o[1].lo);
+  ss.ff_q[k] = make_float2(o[2].hi, o[2].lo);
+  const float alpha = __fadd_rn(o[0].hi, o[0].lo);
+  ss.f_alpha = alpha;
+  ss.alpha_f[k] = alpha;
+  const FF b2 = ff_add(o[1], ff_mul(ff_mul(o[0], o[0]), ff_add(o[2], FF{-2.f, 0.f})));
+  int code = 0;
+  if (!isfinite(alpha) || !isfinite(o[1].hi)) code = 2;
+  else if (!last && b2.hi < 1e-3f * o[1].hi) code = 1;
+  ss.code1 = code;
+  return b2;
+}
+
+// Thread 0: b_{k+1} in FP32 (it only scales complex64 vectors), the breakdown test and the
+// scalars of step k+1, as lz_finish_step.
+__device__ __forceinline__ void lzf_finish_step(SmemSlice& ss, int k, bool last, FF b2, float bd_tol, float& amax,
+                                                float& bmax) {
+  const float beta = __fsqrt_rn(fmaxf(__fadd_rn(b2.hi, b2.lo), 0.f));
+  const float alpha = ss.f_alpha;
+  int stop = 0;
+  if (last) {
+    ss.f_beta_m = beta;
+    stop = 1;
+  } else {
+    amax = fmaxf(amax, fabsf(alpha));
+    if (beta <= bd_tol * fmaxf(1.f, amax + bmax)) {
+      ss.meff = k + 1;
+      ss.broke = 1;
+      stop = 1;
+    } else {
+      bmax = fmaxf(bmax, beta);
+      ss.f_ap = alpha;
+      ss.f_ib = __frcp_rn(beta);
+      ss.f_bk = beta;
+      ss.beta_f[k + 1] = beta;
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(mm[u]), q[u][j], x[j]);
   }
-  if (p.hc_kind == KG_HC_SX_SITE && p.hc_site >= 12) {
-    const float2* q0 = src + (base ^ ((size_t)1 << p.hc_site)) + tid;
-#pragma unroll
-    for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(cu_sx), ldv(q0 + j * NT), x[j]);
+  ss.stop = stop;
+}
+
+// Warp 0 after the last step: the FP64 tridiagonal T (alpha_k, b_{k+1}) from the stored
+// float-float sums, lane k for step k: b_{k+1}^2 from the same identity as lz_after_reduce,
+// or from the explicit ||W - alpha v||^2 where that was formed.
+__device__ __forceinline__ void lzf_build_T(SmemSlice& ss, int m) {
+  const int k = threadIdx.x & 31;
+  const int meff = ss.meff;
+  if (k < meff) {
+    const double al = ff_to_double(FF{ss.ff_a[k].x, ss.ff_a[k].y});
+    double b2;
+    if ((ss.ff_e_set >> k) & 1u) {
+      b2 = ff_to_double(FF{ss.ff_e[k].x, ss.ff_e[k].y});
+    } else {
+      const double nn = ff_to_double(FF{ss.ff_n[k].x, ss.ff_n[k].y});
+      const double q = ff_to_double(FF{ss.ff_q[k].x, ss.ff_q[k].y});
+      b2 = nn - 2.0 * al * al + al * al * q;
+    }
+    const double be = sqrt(fmax(b2, 0.0));
+    ss.alpha[k] = al;
+    if (k + 1 < meff) ss.beta[k + 1] = be;
+    if (k == m - 1) ss.beta_m = be;
   }
+  __syncwarp();
 }
 
 // Lanczos loop of one slice for complex64 tiles of 4096 amplitudes (512 threads x 8), every
@@ -794,8 +871,13 @@ __device__ __forceinline__ void cross_sums64(const EvalParams& p, size_t base, c
 //   bond 8      (bit 8 of tid, bit 0 of j): partner (tid ^ 256) + 512 (j ^ 1)
 //   bonds 9, 10 (bits of j):        partner in registers, test known at compile time
 //   bond 11 and up:                 other tiles (partner sums of W, X recurrence)
-// The partner sums of W_{k+1} are loaded right after the barrier of step k, so their latency
-// overlaps thread 0's FP64 work on alpha_k, b_{k+1}.
+// Where the data lives: v_k of the own tiles in shared memory (the stencil reads the
+// neighbours' amplitudes); X_k and the own W_k, which only their thread reads, in tensor
+// memory; the partner blocks of W_k in a ring of 32 KB bulk copies (TMA) issued by thread 0
+// as soon as the step's scalars are known.  A CTA works tile by tile (partner sums, v_k,
+// stencil), so the blocks of its second tile arrive while the first is computed.  The
+// step's three sums are reduced in float-float; the FP32 scalars that scale the vectors
+// come from them at once, the FP64 tridiagonal after the last step.
 __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, double nrm_src, double uj) {
   const EvalParams& p = *c.p;
   SmemSlice& ss = *c.ss;
@@ -811,137 +893,167 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
   const unsigned xt = (unsigned)(tid ^ (tid >> 1));
   const int t8 = (tid >> 8) & 1;
   const int n_own = c.n_own;
-  // shared memory: v_k of the own tiles (read by neighbours in the stencil), and two
-  // thread-private arrays: X_k and the partner sums of W_k (no synchronisation needed)
+  const float bd_tol = (float)p.bd_tol;
   float2* sv = c.sv[0];
-  float2* sxs = c.sv[1];
-  float2* sx = c.sx;
-  float2 W[NB][APT];  // W_k of the own amplitudes (k = 0: psi); after stage 1: -b_k v_{k-1}
-  double amax = 0.0, bmax = 0.0;  // thread 0: running maxima for the breakdown test
-  if (tid == 0) lz_init(ss, nrm_src, m);
-#pragma unroll
-  for (int cc = 0; cc < NB; ++cc) {
-    if (cc >= n_own) break;
-    const size_t base = c.tile_base(cc);
-    float2 xs[APT];
-    cross_sums64(p, base, src, hxy, cu_sx, xs);
-#pragma unroll
-    for (int j = 0; j < APT; ++j) sxs[cc * T + tid + j * NT] = xs[j];
+  const float2* ring = c.sv[1];
+  const uint32_t tX = c.tm, tW = c.tm + 32u;  // TMEM columns: X of tile cc at tX + 16 cc, W at tW + 16 cc
+  float amax = 0.f, bmax = 0.f;               // thread 0: running maxima for the breakdown test
+  if (tid == 0) {
+    lz_init(ss, nrm_src, m);
+    ss.ff_e_set = 0u;
+    build_chunk_table(c);
   }
+  // W_0 = psi: the own amplitudes into tensor memory
 #pragma unroll
   for (int cc = 0; cc < NB; ++cc) {
     if (cc >= n_own) break;
     const size_t base = c.tile_base(cc);
+    float2 w[APT];
 #pragma unroll
-    for (int j = 0; j < APT; ++j) W[cc][j] = ldv(src + base + tid + j * NT);
+    for (int j = 0; j < APT; ++j) w[j] = ldv(src + base + tid + j * NT);
+    tmem_st8c(tW + 16u * cc, w);
   }
   __syncthreads();
   if (ss.meff == 0) return true;
+  const int ntot = ss.ct_start[2];
+  unsigned gbase = c.lz_count;  // running number of the step's first chunk
+  if (tid == 0) {
+    fence_proxy_async();
+    for (int i = 0; i < ntot && i < kLzStages; ++i) lz_issue(c, src, i, gbase + (unsigned)i);
+  }
+  const float2* vec = src;  // W_k: the vector whose partner blocks the ring holds
   for (int k = 0; k < m; ++k) {
     const bool last = (k == m - 1);
     float2* wdst = last ? nullptr : c.basis_slot(k + 1);  // W_{k+1}: basis slot k+1
     const float ap = ss.f_ap, ib = ss.f_ib, bk = ss.f_bk;
     float2 acc_a = f2(0.f), acc_n = f2(0.f), acc_q = f2(0.f);
-    // ---- stage 1: v_k = (W_k - alpha v_{k-1}) / b_k, X_k = (XS_k - alpha X_{k-1}) / b_k,
-    //      and W <- -b_k v_{k-1}, the first part of W_{k+1}
-#pragma unroll
+#pragma unroll 1
     for (int cc = 0; cc < NB; ++cc) {
       if (cc >= n_own) break;
       const size_t base = c.tile_base(cc);
+      // ---- partner sums XS_k = sum wgt W_k[partner] of this tile, block by block
+      float2 xs[APT];
 #pragma unroll
-      for (int j = 0; j < APT; ++j) {
-        const int li = cc * T + tid + j * NT;
-        const float2 xs = sxs[li];
-        float2 v, x;
-        if (k == 0) {
-          v = f2mul(W[cc][j], f2(ib));
-          x = f2mul(xs, f2(ib));
-          W[cc][j] = f2(0.f);
-        } else {
-          const float2 vp = sv[li];
-          v = f2mul(f2fma(f2(-ap), vp, W[cc][j]), f2(ib));
-          x = f2mul(f2fma(f2(-ap), sx[li], xs), f2(ib));
-          W[cc][j] = f2mul(f2(-bk), vp);
+      for (int j = 0; j < APT; ++j) xs[j] = f2(0.f);
+      const int i1 = ss.ct_start[cc + 1];
+      for (int i = ss.ct_start[cc]; i < i1; ++i) {
+        const unsigned g = gbase + (unsigned)i;
+        const unsigned st = g % kLzStages;
+        const bool ok = mbar_wait_bounded(p, &ss.lmbar[st], (g / kLzStages) & 1u);
+        if (ok) {
+          const unsigned e = ss.ctab[i];
+          const float2 wg = f2((e & 1u) ? cu_sx : hxy);
+          const float2* buf = ring + (size_t)st * T;
+          if (e & 4u) {
+#pragma unroll
+            for (int j = 0; j < APT; ++j) xs[j] = f2fma(wg, buf[tid + j * NT], xs[j]);
+          } else if (e & 2u) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xs[4 + j] = f2fma(wg, buf[tid + j * NT], xs[4 + j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xs[j] = f2fma(wg, buf[tid + j * NT], xs[j]);
+          }
         }
-        sv[li] = v;
-        sx[li] = x;
-      }
-    }
-    __syncthreads();
-    c.mark(0);
-    // ---- stage 2: W_{k+1} = H v_k - b_k v_{k-1}; partial sums
-#pragma unroll
-    for (int cc = 0; cc < NB; ++cc) {
-      if (cc >= n_own) break;
-      const size_t base = c.tile_base(cc);
-      const float2* sc = sv + cc * T;
-      float2 h[APT];
-#pragma unroll
-      for (int j = 0; j < APT; ++j) h[j] = f2(0.f);
-#pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        if ((xt >> b) & 1u) {
-          const float2* ps = sc + (tid ^ (3 << b));
-#pragma unroll
-          for (int j = 0; j < APT; ++j) h[j] = f2add(h[j], ps[j * NT]);
+        if (__syncthreads_or(!ok)) return false;  // every thread is done with stage st
+        if (tid == 0 && i + kLzStages < ntot) {
+          fence_proxy_async();
+          lz_issue(c, vec, i + kLzStages, g + kLzStages);
         }
       }
+      c.mark(0);
+      // ---- stage 1: v_k = (W_k - alpha v_{k-1}) / b_k, X_k = (XS_k - alpha X_{k-1}) / b_k;
+      //      then x <- X_k - b_k v_{k-1}, the part of W_{k+1} that needs no neighbour
+      float2 v[APT], x[APT];
       {
-        const float2* ps = sc + (tid ^ 256);
+        float2 wk[APT], xp[APT];
+        tmem_ld8c(tW + 16u * cc, wk);
+        if (k > 0) tmem_ld8c(tX + 16u * cc, xp);
 #pragma unroll
-        for (int j = 0; j < APT; ++j)
-          if (t8 != (j & 1)) h[j] = f2add(h[j], ps[(j ^ 1) * NT]);
+        for (int j = 0; j < APT; ++j) {
+          const int li = cc * T + tid + j * NT;
+          if (k == 0) {
+            v[j] = f2mul(wk[j], f2(ib));
+            x[j] = f2mul(xs[j], f2(ib));
+          } else {
+            const float2 vp = sv[li];
+            v[j] = f2mul(f2fma(f2(-ap), vp, wk[j]), f2(ib));
+            x[j] = f2mul(f2fma(f2(-ap), xp[j], xs[j]), f2(ib));
+            xp[j] = vp;  // X_{k-1} is no longer needed: keep v_{k-1} in its place
+          }
+          sv[li] = v[j];
+        }
+        tmem_st8c(tX + 16u * cc, x);
+        if (k > 0) {
+#pragma unroll
+          for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(-bk), xp[j], x[j]);
+        }
       }
-      float2 v[APT];
+      __syncthreads();
+      // ---- stage 2: W_{k+1} = H v_k - b_k v_{k-1}; partial sums
+      {
+        const float2* sc = sv + cc * T;
+        float2 h[APT];
 #pragma unroll
-      for (int j = 0; j < APT; ++j) v[j] = sc[tid + j * NT];
+        for (int j = 0; j < APT; ++j) h[j] = f2(0.f);
 #pragma unroll
-      for (int j = 0; j < APT; ++j) {
-        if ((j ^ (j >> 1)) & 1) h[j] = f2add(h[j], v[j ^ 3]);         // bond 9
-        if (((j >> 1) ^ (j >> 2)) & 1) h[j] = f2add(h[j], v[j ^ 6]);  // bond 10
+        for (int b = 0; b < 8; ++b) {
+          if ((xt >> b) & 1u) {
+            const float2* ps = sc + (tid ^ (3 << b));
+#pragma unroll
+            for (int j = 0; j < APT; ++j) h[j] = f2add(h[j], ps[j * NT]);
+          }
+        }
+        {
+          const float2* ps = sc + (tid ^ 256);
+#pragma unroll
+          for (int j = 0; j < APT; ++j)
+            if (t8 != (j & 1)) h[j] = f2add(h[j], ps[(j ^ 1) * NT]);
+        }
+#pragma unroll
+        for (int j = 0; j < APT; ++j) {
+          if ((j ^ (j >> 1)) & 1) h[j] = f2add(h[j], v[j ^ 3]);         // bond 9
+          if (((j >> 1) ^ (j >> 2)) & 1) h[j] = f2add(h[j], v[j ^ 6]);  // bond 10
+        }
+        float2 wv[APT];
+#pragma unroll
+        for (int j = 0; j < APT; ++j) {
+          const int li = tid + j * NT;
+          const unsigned gi = (unsigned)(base + li);
+          const unsigned xg = (gi ^ (gi >> 1)) & c.maskL1;
+          float d = qz * (float)(L1 - 2 * __popc(xg));
+          if (!hc_sx) d += cu_sz * 0.5f * (float)(__popc(mk) - 2 * __popc(gi & mk));
+          float2 w = f2fma(f2(d), v[j], f2fma(f2(hxy), h[j], x[j]));
+          if (hc_sx && hs < 12) w = f2fma(f2(cu_sx), sc[li ^ (1 << hs)], w);
+          acc_a = f2fma(v[j], w, acc_a);
+          acc_n = f2fma(w, w, acc_n);
+          acc_q = f2fma(v[j], v[j], acc_q);
+          wv[j] = w;
+          if (!last) stv(wdst + gi, w);
+        }
+        if (!last) tmem_st8c(tW + 16u * cc, wv);
       }
-#pragma unroll
-      for (int j = 0; j < APT; ++j) {
-        const int li = tid + j * NT;
-        const unsigned gi = (unsigned)(base + li);
-        const unsigned xg = (gi ^ (gi >> 1)) & c.maskL1;
-        float d = qz * (float)(L1 - 2 * __popc(xg));
-        if (!hc_sx) d += cu_sz * 0.5f * (float)(__popc(mk) - 2 * __popc(gi & mk));
-        float2 w = f2fma(f2(d), v[j], f2fma(f2(hxy), h[j], f2add(sx[cc * T + li], W[cc][j])));
-        if (hc_sx && hs < 12) w = f2fma(f2(cu_sx), sc[li ^ (1 << hs)], w);
-        acc_a = f2fma(v[j], w, acc_a);
-        acc_n = f2fma(w, w, acc_n);
-        acc_q = f2fma(v[j], v[j], acc_q);
-        W[cc][j] = w;
-        if (!last) stv(wdst + gi, w);
-      }
+      c.mark(1);
     }
     float acc[3] = {acc_a.x + acc_a.y, acc_n.x + acc_n.y, acc_q.x + acc_q.y};
-    c.mark(1);
-    double out[3];
-    if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
+    if (!reduce_ff_arrive<3>(c.g, ss.red, acc)) return false;
     c.mark(2);
-    // partner sums of W_{k+1} (visible to every CTA after the barrier), then this thread's
-    // own W_{k+1} back from L2; both before the FP64 scalar work of thread 0, so that the
-    // loads overlap it (W is not held in registers across the partner loads)
-    if (!last) {
-#pragma unroll
-      for (int cc = 0; cc < NB; ++cc) {
-        if (cc >= n_own) break;
-        float2 xs[APT];
-        cross_sums64(p, c.tile_base(cc), wdst, hxy, cu_sx, xs);
-#pragma unroll
-        for (int j = 0; j < APT; ++j) sxs[cc * T + tid + j * NT] = xs[j];
-      }
-#pragma unroll
-      for (int cc = 0; cc < NB; ++cc) {
-        if (cc >= n_own) break;
-        const size_t base = c.tile_base(cc);
-#pragma unroll
-        for (int j = 0; j < APT; ++j) W[cc][j] = ldv(wdst + base + tid + j * NT);
+    gbase += (unsigned)ntot;  // every block of step k has been consumed
+    // ---- scalars of step k+1 (warp 0), then the first blocks of W_{k+1}'s partners
+    if (tid < 32) {
+      FF o[3];
+      reduce_ff_collect<3>(c.g, ss.red, o);
+      if (tid == 0) {
+        const FF b2 = lzf_after_reduce(ss, k, last, o);
+        if (ss.code1 == 0) {
+          lzf_finish_step(ss, k, last, b2, bd_tol, amax, bmax);
+          if (!ss.stop) {
+            fence_proxy_async();
+            for (int i = 0; i < ntot && i < kLzStages; ++i) lz_issue(c, wdst, i, gbase + (unsigned)i);
+          }
+        }
       }
     }
-    if (tid == 0) lz_after_reduce(ss, k, last, out);
     __syncthreads();
     const int code = ss.code1;
     if (code == 2) {
@@ -951,22 +1063,39 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
     if (code == 1) {  // near an invariant subspace: explicit ||W - alpha v||^2
       float n1[1] = {0.f};
       const float ra = ss.f_alpha;
-      for (int cc = 0; cc < n_own; ++cc) {
+#pragma unroll
+      for (int cc = 0; cc < NB; ++cc) {
+        if (cc >= n_own) break;
+        float2 wk[APT];
+        tmem_ld8c(tW + 16u * cc, wk);
 #pragma unroll
         for (int j = 0; j < APT; ++j) {
-          const float2 r = f2fma(f2(-ra), sv[cc * T + tid + j * NT], W[cc][j]);
+          const float2 r = f2fma(f2(-ra), sv[cc * T + tid + j * NT], wk[j]);
           n1[0] += r.x * r.x + r.y * r.y;
         }
       }
-      double o1[1];
-      if (!group_reduce<1>(c.g, ss.red, n1, o1)) return false;
-      if (tid == 0) ss.s_b2 = o1[0];
+      if (!reduce_ff_arrive<1>(c.g, ss.red, n1)) return false;
+      if (tid < 32) {
+        FF o1[1];
+        reduce_ff_collect<1>(c.g, ss.red, o1);
+        if (tid == 0) {
+          ss.ff_e[k] = make_float2(o1[0].hi, o1[0].lo);
+          ss.ff_e_set |= 1u << k;
+          lzf_finish_step(ss, k, last, o1[0], bd_tol, amax, bmax);
+          if (!ss.stop) {
+            fence_proxy_async();
+            for (int i = 0; i < ntot && i < kLzStages; ++i) lz_issue(c, wdst, i, gbase + (unsigned)i);
+          }
+        }
+      }
+      __syncthreads();
     }
-    if (tid == 0) lz_finish_step(ss, k, last, p.bd_tol, amax, bmax);
-    __syncthreads();
     c.mark(3);
+    vec = wdst;
     if (ss.stop) break;
   }
+  c.lz_count = gbase;
+  if (tid < 32) lzf_build_T(ss, m);
   return true;
 }
 
@@ -1060,7 +1189,7 @@ __device__ __forceinline__ V* fwd_slot(const Ctx<V>& c, int j) {
 // group of `size` CTAs in which this CTA has rank `rank`.  Returns false if the group aborted.
 template <class V, class A, int APT, int TPC, bool RES, bool FAST>
 __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, SmemSlice& ss,
-                                      unsigned char* smem_dyn, unsigned& ring_count) {
+                                      unsigned char* smem_dyn, unsigned (&rings)[2]) {
   Ctx<V> c;
   c.p = &p;
   c.g.rank = rank;
@@ -1088,7 +1217,9 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
   c.maskL1 = (p.L >= 2) ? ((1u << (p.L - 1)) - 1u) : 0u;
   c.err_max = 0.0;
   c.breakdowns = 0;
-  c.ring_count = ring_count;
+  c.ring_count = rings[0];
+  c.lz_count = rings[1];
+  c.tm = ss.tmem_base + ((((unsigned)threadIdx.x >> 5) & 3u) << 21) + 64u * ((unsigned)threadIdx.x >> 7);
   c.prof_on = (p.prof != nullptr && rank == 0);
   c.prof_last = clock64();
   const long long prof_t0 = c.prof_last;
@@ -1184,21 +1315,42 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
       }
     }
   }
-  ring_count = c.ring_count;
+  rings[0] = c.ring_count;
+  rings[1] = c.lz_count;
   return true;
+}
+
+// Shared prologue/epilogue of the kernels: bulk-copy barriers, and (complex64 resident path)
+// the tensor memory of the CTA, allocated by warp 0 and freed by it on every way out.
+__device__ __forceinline__ void cta_setup(SmemSlice& ss, bool tmem) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kRingStages; ++i) mbar_init(&ss.mbar[i], 1);
+    for (int i = 0; i < kLzStages; ++i) mbar_init(&ss.lmbar[i], 1);
+    fence_mbar_init();
+  }
+  if (tmem) {
+    if (threadIdx.x < 32) tmem_alloc(&ss.tmem_base, kTmemCols);
+    tmem_fence_before_sync();
+  }
+  __syncthreads();
+  if (tmem) tmem_fence_after_sync();
+}
+__device__ __forceinline__ void cta_teardown(SmemSlice& ss, bool tmem) {
+  if (!tmem) return;
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (threadIdx.x < 32) tmem_dealloc(ss.tmem_base, kTmemCols);
 }
 
 template <class V, class A, int APT, int TPC, bool RES, bool FAST>
 __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_constant__ EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kRingStages; ++i) mbar_init(&ss.mbar[i], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  unsigned ring_count = 0;
-  run_eval<V, A, APT, TPC, RES, FAST>(p, blockIdx.x, gridDim.x, ss, smem_dyn, ring_count);
+  cta_setup(ss, FAST);
+  unsigned rings[2] = {0u, 0u};
+  run_eval<V, A, APT, TPC, RES, FAST>(p, blockIdx.x, gridDim.x, ss, smem_dyn, rings);
+  cta_teardown(ss, FAST);
 }
 
 // Many independent problems (complex64) in one cooperative launch.  Every CTA walks its own
@@ -1208,12 +1360,8 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
 __global__ void __launch_bounds__(kThreads, 1) kg_batch_kernel(const __grid_constant__ BatchParams bp) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kRingStages; ++i) mbar_init(&ss.mbar[i], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  unsigned ring_count = 0;
+  cta_setup(ss, true);
+  unsigned rings[2] = {0u, 0u};
   const int i0 = bp.item_off[blockIdx.x], i1 = bp.item_off[blockIdx.x + 1];
   for (int it = i0; it < i1; ++it) {
     const BatchItem item = bp.items[it];
@@ -1225,14 +1373,15 @@ __global__ void __launch_bounds__(kThreads, 1) kg_batch_kernel(const __grid_cons
     const int ntiles = 1 << (p.L - p.t_bits);
     bool ok;
     if (ntiles <= 2 * item.size && p.t_bits == 12)
-      ok = run_eval<float2, float, 8, 2, true, true>(p, item.rank, item.size, ss, smem_dyn, ring_count);
+      ok = run_eval<float2, float, 8, 2, true, true>(p, item.rank, item.size, ss, smem_dyn, rings);
     else if (ntiles <= 2 * item.size)
-      ok = run_eval<float2, float, 8, 2, true, false>(p, item.rank, item.size, ss, smem_dyn, ring_count);
+      ok = run_eval<float2, float, 8, 2, true, false>(p, item.rank, item.size, ss, smem_dyn, rings);
     else
-      ok = run_eval<float2, float, 8, 1, false, false>(p, item.rank, item.size, ss, smem_dyn, ring_count);
-    if (!ok) return;
+      ok = run_eval<float2, float, 8, 1, false, false>(p, item.rank, item.size, ss, smem_dyn, rings);
+    if (!ok) break;
     __syncthreads();
   }
+  cta_teardown(ss, true);
 }
 
 size_t batch_smem_bytes() { return (size_t)3 * 2 * 4096 * sizeof(float2); }
