@@ -660,7 +660,6 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
       }
       if (__syncthreads_or(!ok)) return false;  // every thread is done with stage st
       if (tid == 0 && i + NS < nch) {
-        fence_proxy_async();
         mbar_arrive_expect_tx(&ss.mbar[st], kChunk);
         tma_load_1d(ring + (size_t)st * 4096, chunk_src(i + NS), kChunk, &ss.mbar[st]);
       }
@@ -955,11 +954,10 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
             for (int j = 0; j < 4; ++j) xs[j] = f2fma(wg, buf[tid + j * NT], xs[j]);
           }
         }
-        if (__syncthreads_or(!ok)) return false;  // every thread is done with stage st
-        if (tid == 0 && i + kLzStages < ntot) {
-          fence_proxy_async();
-          lz_issue(c, vec, i + kLzStages, g + kLzStages);
-        }
+        // Every thread is done with stage st: its reads have returned, so the next copy may
+        // overwrite it (no proxy fence: a fence here would wait for the copies in flight).
+        if (__syncthreads_or(!ok)) return false;
+        if (tid == 0 && i + kLzStages < ntot) lz_issue(c, vec, i + kLzStages, g + kLzStages);
       }
       c.mark(0);
       // ---- stage 1: v_k = (W_k - alpha v_{k-1}) / b_k, X_k = (XS_k - alpha X_{k-1}) / b_k;
@@ -1048,7 +1046,7 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
         if (ss.code1 == 0) {
           lzf_finish_step(ss, k, last, b2, bd_tol, amax, bmax);
           if (!ss.stop) {
-            fence_proxy_async();
+            fence_proxy_async_global();  // W_{k+1} of the other CTAs (acquired at the barrier)
             for (int i = 0; i < ntot && i < kLzStages; ++i) lz_issue(c, wdst, i, gbase + (unsigned)i);
           }
         }
@@ -1083,7 +1081,7 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
           ss.ff_e_set |= 1u << k;
           lzf_finish_step(ss, k, last, o1[0], bd_tol, amax, bmax);
           if (!ss.stop) {
-            fence_proxy_async();
+            fence_proxy_async_global();  // W_{k+1} of the other CTAs (acquired at the barrier)
             for (int i = 0; i < ntot && i < kLzStages; ++i) lz_issue(c, wdst, i, gbase + (unsigned)i);
           }
         }
