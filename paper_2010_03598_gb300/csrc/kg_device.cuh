@@ -385,6 +385,71 @@ __device__ __forceinline__ void reduce_ff_collect(Group& g, SmemRed& sm, FF (&ou
   for (int v = 0; v < NV; ++v) out[v] = ff_warp_sum(s[v]);
 }
 
+// Variants for a Group that lives in shared memory, one copy for the whole CTA (the
+// complex64 resident loop keeps it there rather than in every thread's stack frame): only
+// thread 0 writes it.  The barrier advances the reduction parity as well.
+__device__ __forceinline__ bool group_barrier_shared(Group& g, SmemRed& sm) {
+  __syncthreads();  // every thread has read g.phase
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    g.phase++;
+    if (g.skip_arrival) {
+      g.skip_arrival = 0;
+    } else {
+      red_release_add_u64(g.bar, 1ull);
+    }
+    g.epoch++;
+    const unsigned long long goal = g.epoch * (unsigned long long)g.size;
+    unsigned long long t0 = 0;
+    unsigned polls = 0;
+    while (ld_acquire_u64(g.bar) < goal) {
+      if ((++polls & 31u) == 0u) {
+        if (ld_volatile_i32(g.ctrl + kCtrlAbort)) { ok = 0; break; }
+        const unsigned long long now = globaltimer_ns();
+        if (t0 == 0) {
+          t0 = now;
+        } else if ((long long)(now - t0) > g.wait_limit_ns) {
+          atomicCAS(g.ctrl + kCtrlStatus, 0, (int)KG_ERR_TIMEOUT);
+          atomicExch(g.ctrl + kCtrlAbort, 1);
+          ok = 0;
+          break;
+        }
+        if (polls > 4096u) __nanosleep(64);
+      }
+    }
+    sm.flag = ok;
+  }
+  __syncthreads();
+  return sm.flag != 0;
+}
+template <int NV>
+__device__ __forceinline__ bool reduce_ff_arrive_shared(Group& g, SmemRed& sm, float (&vals)[NV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
+  }
+  __syncthreads();
+  const int size = g.size;
+  if (warp < NV) {
+    FF s{(lane < nw) ? sm.warp_part_f[lane * kNRed + warp] : 0.f, 0.f};
+    s = ff_warp_sum(s);
+    if (lane == 0) {
+      if (size > 1) {
+        float2* slots = reinterpret_cast<float2*>(g.red + (size_t)(g.phase & 1) * g.stride * kNRed);
+        __stcg(slots + (size_t)g.rank * kNRed + warp, make_float2(s.hi, s.lo));
+      } else {
+        sm.cta_ff[warp] = make_float2(s.hi, s.lo);
+      }
+    }
+  }
+  if (size > 1) return group_barrier_shared(g, sm);
+  __syncthreads();
+  return ld_volatile_i32(g.ctrl + kCtrlAbort) == 0;
+}
+
 // ---------------------------------------------------------------- small exponential
 // 1/p! for p = 0..40 (exact rationals rounded once by the compiler).
 __device__ __constant__ double kInvFact[41] = {

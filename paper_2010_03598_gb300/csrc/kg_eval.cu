@@ -38,7 +38,19 @@ static_assert((1 << kLogNT) == kThreads, "kLogNT must match kThreads");
 constexpr int kRingStages = 6;  // 6 x 32 KB: all of the resident path's shared memory
 constexpr int kLzStages = 4;    // Lanczos partner ring: 4 x 32 KB behind the 64 KB of v_k
 constexpr int kLzMaxChunks = 2 * (1 + (kMaxL - 13) + 1);  // two tiles: bond 11, outer bonds, Sx site
-constexpr uint32_t kTmemCols = 256;  // X and W of two tiles: 64 columns per warp, 4 warps per lane quarter
+constexpr uint32_t kTmemCols = 512;  // 128 columns per warp, 4 warps per lane quarter
+
+// What the complex64 resident loop reads in its steps, per CTA (shared memory).
+struct ResCtx {
+  size_t tbase[2];   // own tiles' first amplitude
+  float2* basis;     // basis slot 1 (slot k at basis + (k - 1) D)
+  size_t D;
+  float2* sw;        // W_k of the own tiles (shared memory)
+  float2* ring;      // partner-block ring (shared memory)
+  unsigned maskL1, mk;
+  int L1, hs, hcsx, n_own, m;
+  float hxy, qz, cusx, cusz, amax, bmax, bdtol;
+};
 
 struct SmemSlice {
   SmemRed red;
@@ -61,6 +73,10 @@ struct SmemSlice {
   unsigned long long lmbar[kLzStages];
   unsigned ctab[kLzMaxChunks];
   int ct_start[3];
+  int first;  // the own tile computed first (more partner blocks)
+  long long prof_last, prof_acc[8];  // phase timing (thread 0 of CTA 0)
+  ResCtx r;   // the resident loop's per-slice constants
+  Group grp;  // the group's barrier state while the resident loop runs (written by thread 0)
   float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
   unsigned ff_e_set;
   uint32_t tmem_base;
@@ -163,6 +179,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(const EvalParams& p, unsigned 
   }
 }
 
+// Phase timing (thread 0 of CTA 0): cycles since the previous mark go to counter `phase`.
+__device__ __forceinline__ void prof_mark(SmemSlice& ss, int phase) {
+  const long long now = clock64();
+  ss.prof_acc[phase] += now - ss.prof_last;
+  ss.prof_last = now;
+}
+
 template <class V>
 struct Ctx {
   using R = typename VecTraits<V>::R;
@@ -180,17 +203,11 @@ struct Ctx {
   int breakdowns;
   unsigned ring_count;   // recombination bulk copies consumed so far (ring stage and phase parity)
   unsigned lz_count;     // Lanczos partner bulk copies consumed so far (complex64 resident path)
-  uint32_t tm;           // this warp's TMEM address: its lane quarter, its 64-column group
-  bool prof_on;          // phase timing (CTA 0, thread 0)
-  long long prof_last;
-  long long prof_acc[8];
+  uint32_t tm;           // this warp's TMEM address: its lane quarter, its 128-column group
+  bool prof_on;          // phase timing (CTA 0, thread 0; the counters are in shared memory)
 
   __device__ __forceinline__ void mark(int phase) {
-    if (prof_on && threadIdx.x == 0) {
-      const long long now = clock64();
-      prof_acc[phase] += now - prof_last;
-      prof_last = now;
-    }
+    if (prof_on && threadIdx.x == 0) prof_mark(*ss, phase);
   }
   __device__ V* basis_slot(int k) const { return (V*)p->basis + (size_t)(k - 1) * D; }
   __device__ V* wbuf(int k) const { return (V*)p->wbuf + (size_t)(k & 1) * D; }
@@ -753,11 +770,11 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return _
 //   an Sx control on site s >= 12: tile base ^ (1 << s), element for element.
 // Entry: bits 3.. = source offset in units of 2048 amplitudes (16 KB), bit 2 = whole tile
 // (32 KB, feeds every own amplitude) rather than one half, bit 1 = the own half h fed by a
-// half block, bit 0 = weight of the Sx control instead of Jxy/2.  Tile 0's entries come
-// first, then tile 1's: the ring fetches tile 1's blocks while tile 0 is being computed.
-__device__ __forceinline__ void build_chunk_table(const Ctx<float2>& c) {
-  const EvalParams& p = *c.p;
-  SmemSlice& ss = *c.ss;
+// half block, bit 0 = weight of the Sx control instead of Jxy/2.  ct_start[cc] .. ct_start[cc+1]
+// are tile cc's entries.  `first` is the tile with more blocks: the CTA computes it first,
+// from plain loads issued right after the barrier, while the other tile's blocks stream
+// into the bulk-copy ring.
+__device__ __forceinline__ void build_chunk_table(const Ctx<float2>& c, const EvalParams& p, SmemSlice& ss) {
   const int L1 = p.L - 1;
   int n = 0;
   ss.ct_start[0] = 0;
@@ -777,17 +794,43 @@ __device__ __forceinline__ void build_chunk_table(const Ctx<float2>& c) {
     }
     ss.ct_start[cc + 1] = n;
   }
+  ss.first = (c.n_own == 2 && ss.ct_start[2] - ss.ct_start[1] > ss.ct_start[1]) ? 1 : 0;
+}
+
+// First table entry and number of blocks of the tile whose blocks go through the ring.
+__device__ __forceinline__ int ring_i0(const SmemSlice& ss) { return ss.ct_start[ss.first ^ 1]; }
+__device__ __forceinline__ int ring_n(const SmemSlice& ss) {
+  return (ss.r.n_own == 2) ? ss.ct_start[(ss.first ^ 1) + 1] - ss.ct_start[ss.first ^ 1] : 0;
 }
 
 // Thread 0: bulk copy of chunk i of the table from vector `vec` into ring stage g % stages
-// (g = the chunk's running number), completing on that stage's barrier.
-__device__ __forceinline__ void lz_issue(const Ctx<float2>& c, const float2* vec, int i, unsigned g) {
-  SmemSlice& ss = *c.ss;
+// (g = the copy's running number), completing on that stage's barrier.
+__device__ __forceinline__ void lz_issue(SmemSlice& ss, const float2* vec, int i, unsigned g) {
   const unsigned e = ss.ctab[i];
   const unsigned st = g % kLzStages;
   const uint32_t bytes = (e & 4u) ? 32768u : 16384u;
   mbar_arrive_expect_tx(&ss.lmbar[st], bytes);
-  tma_load_1d(c.sv[1] + (size_t)st * 4096, vec + ((size_t)(e >> 3) << 11), bytes, &ss.lmbar[st]);
+  tma_load_1d(ss.r.ring + (size_t)st * 4096, vec + ((size_t)(e >> 3) << 11), bytes, &ss.lmbar[st]);
+}
+
+// Thread 0: the first ring copies of the second tile's blocks of vector vec (written by the
+// group before the barrier this thread has just passed).
+__device__ __forceinline__ void ring_start(SmemSlice& ss, const float2* vec, unsigned gbase) {
+  fence_proxy_async_global();
+  const int i0 = ring_i0(ss), n = ring_n(ss);
+  for (int r = 0; r < n && r < kLzStages; ++r) lz_issue(ss, vec, i0 + r, gbase + (unsigned)r);
+}
+
+// Every thread: wait for ring copies that were started but will not be consumed (the loop
+// ends early); true if they all arrived in time.
+__device__ __forceinline__ bool ring_drain(const EvalParams& p, SmemSlice& ss, unsigned gbase) {
+  bool ok = true;
+  const int n = ring_n(ss);
+  for (int r = 0; r < n && r < kLzStages; ++r) {
+    const unsigned g = gbase + (unsigned)r;
+    ok = ok && mbar_wait_bounded(p, &ss.lmbar[g % kLzStages], (g / kLzStages) & 1u);
+  }
+  return ok;
 }
 
 // Thread 0, complex64 resident path: alpha_k and b_{k+1}^2 = ||W||^2 + alpha^2 (||v||^2 - 2)
@@ -860,138 +903,177 @@ __device__ __forceinline__ void lzf_build_T(SmemSlice& ss, int m) {
   __syncwarp();
 }
 
+// Warp 0 after the barrier that closed step k: float-float totals of the step's sums, then
+// thread 0 sets alpha_k, b_{k+1} and the scalars of step k+1.
+__device__ __forceinline__ void warp0_scalars(SmemSlice& ss, int k, bool last) {
+  FF o[3];
+  reduce_ff_collect<3>(ss.grp, ss.red, o);
+  if (threadIdx.x == 0) {
+    const FF b2 = lzf_after_reduce(ss, k, last, o);
+    if (ss.code1 == 0) lzf_finish_step(ss, k, last, b2, ss.r.bdtol, ss.r.amax, ss.r.bmax);
+  }
+}
+
+// Partner sums xs += sum wgt W[partner] of one tile from vector pv (table entries i0 .. i1),
+// three blocks in flight in registers.
+__device__ __forceinline__ void partner_regs(const SmemSlice& ss, const float2* pv, int i0, int i1, float2 (&xs)[8]) {
+  constexpr int APT = 8, NT = kThreads, G = 3;
+  const int tid = threadIdx.x;
+  const float hxy = ss.r.hxy, cu_sx = ss.r.cusx;
+  for (int ib = i0; ib < i1; ib += G) {
+    float2 q[G][APT];
+    float wq[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int i = ib + u;
+      const unsigned e = (i < i1) ? ss.ctab[i] : 0u;
+      // own amplitude j reads sb[j * NT]: the block itself, or for a half block feeding own
+      // half h, the block shifted down by h * 2048 (only j in [4h, 4h + 4) are read)
+      const unsigned hm = (i >= i1) ? 0u : ((e & 4u) ? 0xffu : (((e >> 1) & 1u) ? 0xf0u : 0x0fu));
+      wq[u] = (e & 1u) ? cu_sx : hxy;
+      const long long off = ((long long)(e >> 3) << 11) + tid - (((e & 6u) == 2u) ? 4 * NT : 0);
+      const float2* sb = pv + off;
+#pragma unroll
+      for (int j = 0; j < APT; ++j) q[u][j] = ((hm >> j) & 1u) ? ldv(sb + j * NT) : f2(0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+#pragma unroll
+      for (int j = 0; j < APT; ++j) xs[j] = f2fma(f2(wq[u]), q[u][j], xs[j]);
+  }
+}
+
 // Lanczos loop of one slice for complex64 tiles of 4096 amplitudes (512 threads x 8), every
-// CTA holding its (at most 2) tiles resident.  Same recurrence as lanczos_generic, except
-// that the basis slots hold the raw vectors W_k (slot 0: psi) rather than v_k: they are
-// written anyway for the other tiles' partners, and since v_k = (W_k - alpha v_{k-1}) / b_k
-// the recombination sum_k c_k v_k is a sum over the W_k with transformed coefficients.  The
-// amplitude of thread tid in register j is li = tid + 512 j, so
+// CTA holding its (at most 2) tiles resident.  Same recurrence as lanczos_generic, in
+// another arrangement of the same arithmetic: the stencil acts on the raw vector W_k, which
+// needs none of the step's scalars,
+//   H W_k     = diag W_k + (Jxy/2) sum_{bonds} W_k[partner]   (+ control)
+//   v_k       = (W_k - alpha_{k-1} v_{k-1}) / b_k
+//   H v_k     = (H W_k - alpha_{k-1} H v_{k-1}) / b_k
+//   W_{k+1}   = H v_k - b_k v_{k-1}
+//   alpha_k   = <v_k|W_{k+1}>,  b_{k+1}^2 = ||W_{k+1}||^2 - 2 alpha_k <v_k|W_{k+1}> + alpha_k^2 ||v_k||^2,
+// so the stencil of a step runs while warp 0 is still collecting the previous step's sums.
+// The basis slots hold the raw vectors W_k (slot 0: psi): they are written anyway for the
+// other tiles' partners, and the recombination sum_k c_k v_k is a sum over the W_k with
+// transformed coefficients.  The amplitude of thread tid in register j is li = tid + 512 j:
 //   bonds 0..7  (bits inside tid):  antiparallel test shared by all j, partner (tid ^ 3<<b) + 512 j
 //   bond 8      (bit 8 of tid, bit 0 of j): partner (tid ^ 256) + 512 (j ^ 1)
 //   bonds 9, 10 (bits of j):        partner in registers, test known at compile time
-//   bond 11 and up:                 other tiles (partner sums of W, X recurrence)
-// Where the data lives: v_k of the own tiles in shared memory (the stencil reads the
-// neighbours' amplitudes); X_k and the own W_k, which only their thread reads, in tensor
-// memory; the partner blocks of W_k in a ring of 32 KB bulk copies (TMA) issued by thread 0
-// as soon as the step's scalars are known.  A CTA works tile by tile (partner sums, v_k,
-// stencil), so the blocks of its second tile arrive while the first is computed.  The
-// step's three sums are reduced in float-float; the FP32 scalars that scale the vectors
-// come from them at once, the FP64 tridiagonal after the last step.
+//   bond 11 and up:                 other tiles' blocks of W_k (global memory)
+// Where the data lives: W_k of the own tiles in shared memory (the stencil reads the
+// neighbours' amplitudes); v_{k-1} and H v_{k-1}, which only their thread reads, in tensor
+// memory; the slice's constants and the group's barrier state in shared memory (the L1 left
+// beside 200 KB of shared memory is too small for per-thread stack frames).  Partner
+// blocks: for the tile with more blocks, plain L2 loads into registers, three blocks in
+// flight, right after the barrier; for the other tile, a ring of 32 KB bulk copies (TMA)
+// that thread 0 starts at the barrier and that fills while the first tile is computed.  The
+// step's three sums are reduced in float-float; the FP32 scalars that scale the vectors come
+// from them at once, the FP64 tridiagonal after the last step.
 __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, double nrm_src, double uj) {
   const EvalParams& p = *c.p;
   SmemSlice& ss = *c.ss;
   constexpr int APT = 8, NB = 2, T = 4096, NT = kThreads;
-  const int m = p.m;
   const int tid = threadIdx.x;
-  const float hxy = (float)(0.5 * p.Jxy), qz = (float)(0.25 * p.Jz);
-  const float cu_sx = (float)(0.5 * uj * p.hc_amp), cu_sz = (float)(uj * p.hc_amp);
-  const unsigned mk = (unsigned)p.hc_mask;
-  const bool hc_sx = (p.hc_kind == KG_HC_SX_SITE);
-  const int hs = p.hc_site;
-  const int L1 = p.L - 1;
   const unsigned xt = (unsigned)(tid ^ (tid >> 1));
   const int t8 = (tid >> 8) & 1;
-  const int n_own = c.n_own;
-  const float bd_tol = (float)p.bd_tol;
-  float2* sv = c.sv[0];
-  const float2* ring = c.sv[1];
-  const uint32_t tX = c.tm, tW = c.tm + 32u;  // TMEM columns: X of tile cc at tX + 16 cc, W at tW + 16 cc
-  float amax = 0.f, bmax = 0.f;               // thread 0: running maxima for the breakdown test
+  const bool prof = c.prof_on && tid == 0;
+  // TMEM columns: v_{k-1} of tile cc at tV + 16 cc, H v_{k-1} at tH + 16 cc, and H W_k of the
+  // tile in hand at tP while the step's scalars are formed
+  const uint32_t tV = c.tm, tH = c.tm + 32u, tP = c.tm + 64u;
   if (tid == 0) {
-    lz_init(ss, nrm_src, m);
+    ResCtx& r = ss.r;
+    r.tbase[0] = c.tile_base(0);
+    r.tbase[1] = (c.n_own > 1) ? c.tile_base(1) : 0;
+    r.basis = (float2*)p.basis;
+    r.D = c.D;
+    r.sw = c.sv[0];
+    r.ring = c.sv[1];
+    r.maskL1 = c.maskL1;
+    r.mk = (unsigned)p.hc_mask;
+    r.L1 = p.L - 1;
+    r.hs = p.hc_site;
+    r.hcsx = (p.hc_kind == KG_HC_SX_SITE) ? 1 : 0;
+    r.n_own = c.n_own;
+    r.m = p.m;
+    r.hxy = (float)(0.5 * p.Jxy);
+    r.qz = (float)(0.25 * p.Jz);
+    r.cusx = (float)(0.5 * uj * p.hc_amp);
+    r.cusz = (float)(uj * p.hc_amp);
+    r.amax = 0.f;  // running maxima for the breakdown test
+    r.bmax = 0.f;
+    r.bdtol = (float)p.bd_tol;
+    ss.grp = c.g;
+    lz_init(ss, nrm_src, p.m);
     ss.ff_e_set = 0u;
-    build_chunk_table(c);
+    build_chunk_table(c, p, ss);
   }
-  // W_0 = psi: the own amplitudes into tensor memory
+  // W_0 = psi: the own amplitudes into shared memory
+  {
+    float2* sw = c.sv[0];
 #pragma unroll
-  for (int cc = 0; cc < NB; ++cc) {
-    if (cc >= n_own) break;
-    const size_t base = c.tile_base(cc);
-    float2 w[APT];
+    for (int cc = 0; cc < NB; ++cc) {
+      if (cc >= c.n_own) break;
+      const size_t base = c.tile_base(cc);
 #pragma unroll
-    for (int j = 0; j < APT; ++j) w[j] = ldv(src + base + tid + j * NT);
-    tmem_st8c(tW + 16u * cc, w);
+      for (int j = 0; j < APT; ++j) sw[cc * T + tid + j * NT] = ldv(src + base + tid + j * NT);
+    }
   }
   __syncthreads();
   if (ss.meff == 0) return true;
-  const int ntot = ss.ct_start[2];
-  unsigned gbase = c.lz_count;  // running number of the step's first chunk
-  if (tid == 0) {
-    fence_proxy_async();
-    for (int i = 0; i < ntot && i < kLzStages; ++i) lz_issue(c, src, i, gbase + (unsigned)i);
-  }
-  const float2* vec = src;  // W_k: the vector whose partner blocks the ring holds
+  const int m = ss.r.m;
+  unsigned gbase = c.lz_count;  // running number of the step's first ring copy
+  if (tid == 0 && ring_n(ss) > 0) ring_start(ss, src, gbase);
+  const float2* vec = src;  // W_k: the vector whose partner blocks are read in step k
+  bool done = false;        // the loop ran all m steps (the last step's sums still to collect)
   for (int k = 0; k < m; ++k) {
     const bool last = (k == m - 1);
-    float2* wdst = last ? nullptr : c.basis_slot(k + 1);  // W_{k+1}: basis slot k+1
-    const float ap = ss.f_ap, ib = ss.f_ib, bk = ss.f_bk;
+    float2* wdst = last ? nullptr : ss.r.basis + (size_t)k * ss.r.D;  // W_{k+1}: basis slot k+1
     float2 acc_a = f2(0.f), acc_n = f2(0.f), acc_q = f2(0.f);
+    bool stopped = false;
 #pragma unroll 1
-    for (int cc = 0; cc < NB; ++cc) {
-      if (cc >= n_own) break;
-      const size_t base = c.tile_base(cc);
-      // ---- partner sums XS_k = sum wgt W_k[partner] of this tile, block by block
+    for (int qq = 0; qq < NB; ++qq) {
+      if (qq >= ss.r.n_own) break;
+      const int cc = ss.first ^ qq;
+      // ---- partner sums of W_k for this tile
       float2 xs[APT];
 #pragma unroll
       for (int j = 0; j < APT; ++j) xs[j] = f2(0.f);
-      const int i1 = ss.ct_start[cc + 1];
-      for (int i = ss.ct_start[cc]; i < i1; ++i) {
-        const unsigned g = gbase + (unsigned)i;
-        const unsigned st = g % kLzStages;
-        const bool ok = mbar_wait_bounded(p, &ss.lmbar[st], (g / kLzStages) & 1u);
-        if (ok) {
-          const unsigned e = ss.ctab[i];
-          const float2 wg = f2((e & 1u) ? cu_sx : hxy);
-          const float2* buf = ring + (size_t)st * T;
-          if (e & 4u) {
+      if (qq == 0) {
+        partner_regs(ss, vec, ss.ct_start[cc], ss.ct_start[cc + 1], xs);
+      } else {
+        const int iB0 = ss.ct_start[cc], nB = ss.ct_start[cc + 1] - iB0;
+        const float2* ring = ss.r.ring;
+        for (int r = 0; r < nB; ++r) {
+          const unsigned g = gbase + (unsigned)r;
+          const unsigned st = g % kLzStages;
+          const bool ok = mbar_wait_bounded(p, &ss.lmbar[st], (g / kLzStages) & 1u);
+          if (ok) {
+            const unsigned e = ss.ctab[iB0 + r];
+            const float2 wg = f2((e & 1u) ? ss.r.cusx : ss.r.hxy);
+            const float2* buf = ring + (size_t)st * T;
+            if (e & 4u) {
 #pragma unroll
-            for (int j = 0; j < APT; ++j) xs[j] = f2fma(wg, buf[tid + j * NT], xs[j]);
-          } else if (e & 2u) {
+              for (int j = 0; j < APT; ++j) xs[j] = f2fma(wg, buf[tid + j * NT], xs[j]);
+            } else if (e & 2u) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) xs[4 + j] = f2fma(wg, buf[tid + j * NT], xs[4 + j]);
-          } else {
+              for (int j = 0; j < 4; ++j) xs[4 + j] = f2fma(wg, buf[tid + j * NT], xs[4 + j]);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) xs[j] = f2fma(wg, buf[tid + j * NT], xs[j]);
+              for (int j = 0; j < 4; ++j) xs[j] = f2fma(wg, buf[tid + j * NT], xs[j]);
+            }
           }
-        }
-        // Every thread is done with stage st: its reads have returned, so the next copy may
-        // overwrite it (no proxy fence: a fence here would wait for the copies in flight).
-        if (__syncthreads_or(!ok)) return false;
-        if (tid == 0 && i + kLzStages < ntot) lz_issue(c, vec, i + kLzStages, g + kLzStages);
-      }
-      c.mark(0);
-      // ---- stage 1: v_k = (W_k - alpha v_{k-1}) / b_k, X_k = (XS_k - alpha X_{k-1}) / b_k;
-      //      then x <- X_k - b_k v_{k-1}, the part of W_{k+1} that needs no neighbour
-      float2 v[APT], x[APT];
-      {
-        float2 wk[APT], xp[APT];
-        tmem_ld8c(tW + 16u * cc, wk);
-        if (k > 0) tmem_ld8c(tX + 16u * cc, xp);
-#pragma unroll
-        for (int j = 0; j < APT; ++j) {
-          const int li = cc * T + tid + j * NT;
-          if (k == 0) {
-            v[j] = f2mul(wk[j], f2(ib));
-            x[j] = f2mul(xs[j], f2(ib));
-          } else {
-            const float2 vp = sv[li];
-            v[j] = f2mul(f2fma(f2(-ap), vp, wk[j]), f2(ib));
-            x[j] = f2mul(f2fma(f2(-ap), xp[j], xs[j]), f2(ib));
-            xp[j] = vp;  // X_{k-1} is no longer needed: keep v_{k-1} in its place
-          }
-          sv[li] = v[j];
-        }
-        tmem_st8c(tX + 16u * cc, x);
-        if (k > 0) {
-#pragma unroll
-          for (int j = 0; j < APT; ++j) x[j] = f2fma(f2(-bk), xp[j], x[j]);
+          // Every thread is done with stage st: its reads have returned, so the next copy may
+          // overwrite it (no proxy fence: a fence here would wait for the copies in flight).
+          if (__syncthreads_or(!ok)) return false;
+          if (tid == 0 && r + kLzStages < nB) lz_issue(ss, vec, iB0 + r + kLzStages, g + kLzStages);
         }
       }
-      __syncthreads();
-      // ---- stage 2: W_{k+1} = H v_k - b_k v_{k-1}; partial sums
+      if (prof) prof_mark(ss, 0);
+      // ---- stencil: hw = H W_k on the own amplitudes (parked in TMEM across the barrier)
       {
-        const float2* sc = sv + cc * T;
-        float2 h[APT];
+        const size_t base = ss.r.tbase[cc];
+        const float2* sc = ss.r.sw + cc * T;
+        float2 h[APT], wo[APT], hw[APT];
 #pragma unroll
         for (int j = 0; j < APT; ++j) h[j] = f2(0.f);
 #pragma unroll
@@ -1009,90 +1091,139 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
             if (t8 != (j & 1)) h[j] = f2add(h[j], ps[(j ^ 1) * NT]);
         }
 #pragma unroll
+        for (int j = 0; j < APT; ++j) wo[j] = sc[tid + j * NT];
+#pragma unroll
         for (int j = 0; j < APT; ++j) {
-          if ((j ^ (j >> 1)) & 1) h[j] = f2add(h[j], v[j ^ 3]);         // bond 9
-          if (((j >> 1) ^ (j >> 2)) & 1) h[j] = f2add(h[j], v[j ^ 6]);  // bond 10
+          if ((j ^ (j >> 1)) & 1) h[j] = f2add(h[j], wo[j ^ 3]);         // bond 9
+          if (((j >> 1) ^ (j >> 2)) & 1) h[j] = f2add(h[j], wo[j ^ 6]);  // bond 10
         }
-        float2 wv[APT];
+        const float hxy = ss.r.hxy, qz = ss.r.qz, cu_sx = ss.r.cusx, cu_sz = ss.r.cusz;
+        const unsigned mk = ss.r.mk, maskL1 = ss.r.maskL1;
+        const bool hc_sx = ss.r.hcsx != 0;
+        const int hs = ss.r.hs, L1 = ss.r.L1;
 #pragma unroll
         for (int j = 0; j < APT; ++j) {
           const int li = tid + j * NT;
           const unsigned gi = (unsigned)(base + li);
-          const unsigned xg = (gi ^ (gi >> 1)) & c.maskL1;
+          const unsigned xg = (gi ^ (gi >> 1)) & maskL1;
           float d = qz * (float)(L1 - 2 * __popc(xg));
           if (!hc_sx) d += cu_sz * 0.5f * (float)(__popc(mk) - 2 * __popc(gi & mk));
-          float2 w = f2fma(f2(d), v[j], f2fma(f2(hxy), h[j], x[j]));
-          if (hc_sx && hs < 12) w = f2fma(f2(cu_sx), sc[li ^ (1 << hs)], w);
-          acc_a = f2fma(v[j], w, acc_a);
-          acc_n = f2fma(w, w, acc_n);
-          acc_q = f2fma(v[j], v[j], acc_q);
-          wv[j] = w;
-          if (!last) stv(wdst + gi, w);
+          float2 hv = f2fma(f2(d), wo[j], f2fma(f2(hxy), h[j], xs[j]));
+          if (hc_sx && hs < 12) hv = f2fma(f2(cu_sx), sc[li ^ (1 << hs)], hv);
+          hw[j] = hv;
         }
-        if (!last) tmem_st8c(tW + 16u * cc, wv);
+        tmem_st8c(tP, hw);
       }
-      c.mark(1);
-    }
-    float acc[3] = {acc_a.x + acc_a.y, acc_n.x + acc_n.y, acc_q.x + acc_q.y};
-    if (!reduce_ff_arrive<3>(c.g, ss.red, acc)) return false;
-    c.mark(2);
-    gbase += (unsigned)ntot;  // every block of step k has been consumed
-    // ---- scalars of step k+1 (warp 0), then the first blocks of W_{k+1}'s partners
-    if (tid < 32) {
-      FF o[3];
-      reduce_ff_collect<3>(c.g, ss.red, o);
-      if (tid == 0) {
-        const FF b2 = lzf_after_reduce(ss, k, last, o);
-        if (ss.code1 == 0) {
-          lzf_finish_step(ss, k, last, b2, bd_tol, amax, bmax);
-          if (!ss.stop) {
-            fence_proxy_async_global();  // W_{k+1} of the other CTAs (acquired at the barrier)
-            for (int i = 0; i < ntot && i < kLzStages; ++i) lz_issue(c, wdst, i, gbase + (unsigned)i);
+      if (qq == 0 && k > 0 && tid < 32) warp0_scalars(ss, k - 1, false);
+      __syncthreads();  // the scalars of step k; every neighbour read of W_k in this tile done
+      if (qq == 0 && k > 0) {
+        const int code = ss.code1;
+        if (code == 2) {
+          if (tid == 0) flag_nonfinite(p);
+          ring_drain(p, ss, gbase);
+          return false;
+        }
+        if (code == 1) {  // near an invariant subspace: explicit ||W_k - alpha_{k-1} v_{k-1}||^2
+          float n1[1] = {0.f};
+          const float ra = ss.f_alpha;
+          for (int c2 = 0; c2 < ss.r.n_own; ++c2) {
+            float2 vp[APT];
+            tmem_ld8c(tV + 16u * c2, vp);
+#pragma unroll
+            for (int j = 0; j < APT; ++j) {
+              const float2 rr = f2fma(f2(-ra), vp[j], ss.r.sw[c2 * T + tid + j * NT]);
+              n1[0] += rr.x * rr.x + rr.y * rr.y;
+            }
+          }
+          if (!reduce_ff_arrive_shared<1>(ss.grp, ss.red, n1)) {
+            ring_drain(p, ss, gbase);
+            return false;
+          }
+          if (tid < 32) {
+            FF o1[1];
+            reduce_ff_collect<1>(ss.grp, ss.red, o1);
+            if (tid == 0) {
+              ss.ff_e[k - 1] = make_float2(o1[0].hi, o1[0].lo);
+              ss.ff_e_set |= 1u << (k - 1);
+              lzf_finish_step(ss, k - 1, false, o1[0], ss.r.bdtol, ss.r.amax, ss.r.bmax);
+            }
+          }
+          __syncthreads();
+        }
+        if (ss.stop) {  // breakdown: v_k does not exist; the copies started for step k are not used
+          if (__syncthreads_or(!ring_drain(p, ss, gbase))) return false;
+          gbase += (unsigned)min(ring_n(ss), kLzStages);
+          stopped = true;
+          break;
+        }
+      }
+      if (prof) prof_mark(ss, 3);
+      // ---- v_k, H v_k, W_{k+1} = H v_k - b_k v_{k-1} for the own amplitudes; partial sums
+      {
+        const float ap = ss.f_ap, ib = ss.f_ib, bk = ss.f_bk;
+        float2* sw = ss.r.sw + cc * T;
+        float2 vp[APT], hp[APT], wo[APT], hw[APT];
+        tmem_ld8c(tP, hw);
+#pragma unroll
+        for (int j = 0; j < APT; ++j) wo[j] = sw[tid + j * NT];  // W_k, own amplitudes
+        if (k > 0) {
+          tmem_ld8c(tV + 16u * cc, vp);
+          tmem_ld8c(tH + 16u * cc, hp);
+        }
+#pragma unroll
+        for (int j = 0; j < APT; ++j) {
+          float2 v, hv, w;
+          if (k == 0) {
+            v = f2mul(wo[j], f2(ib));
+            hv = f2mul(hw[j], f2(ib));
+            w = hv;
+          } else {
+            v = f2mul(f2fma(f2(-ap), vp[j], wo[j]), f2(ib));
+            hv = f2mul(f2fma(f2(-ap), hp[j], hw[j]), f2(ib));
+            w = f2fma(f2(-bk), vp[j], hv);
+          }
+          acc_a = f2fma(v, w, acc_a);
+          acc_n = f2fma(w, w, acc_n);
+          acc_q = f2fma(v, v, acc_q);
+          vp[j] = v;
+          hp[j] = hv;
+          wo[j] = w;
+        }
+        if (!last) {
+          tmem_st8c(tV + 16u * cc, vp);
+          tmem_st8c(tH + 16u * cc, hp);
+          const size_t base = ss.r.tbase[cc];
+#pragma unroll
+          for (int j = 0; j < APT; ++j) {
+            const int li = tid + j * NT;
+            sw[li] = wo[j];
+            stv(wdst + base + li, wo[j]);
           }
         }
       }
+      if (prof) prof_mark(ss, 1);
     }
+    if (stopped) break;
+    float acc[3] = {acc_a.x + acc_a.y, acc_n.x + acc_n.y, acc_q.x + acc_q.y};
+    if (!reduce_ff_arrive_shared<3>(ss.grp, ss.red, acc)) return false;
+    if (prof) prof_mark(ss, 2);
+    gbase += (unsigned)ring_n(ss);  // every ring copy of step k has been consumed
+    if (!last && tid == 0 && ring_n(ss) > 0) ring_start(ss, wdst, gbase);
+    vec = wdst;
+    if (last) done = true;
+  }
+  if (done) {  // the sums of the last step: alpha_{m-1}, b_m (error indicator)
+    if (tid < 32) warp0_scalars(ss, m - 1, true);
     __syncthreads();
-    const int code = ss.code1;
-    if (code == 2) {
+    if (ss.code1 == 2) {
       if (tid == 0) flag_nonfinite(p);
       return false;
     }
-    if (code == 1) {  // near an invariant subspace: explicit ||W - alpha v||^2
-      float n1[1] = {0.f};
-      const float ra = ss.f_alpha;
-#pragma unroll
-      for (int cc = 0; cc < NB; ++cc) {
-        if (cc >= n_own) break;
-        float2 wk[APT];
-        tmem_ld8c(tW + 16u * cc, wk);
-#pragma unroll
-        for (int j = 0; j < APT; ++j) {
-          const float2 r = f2fma(f2(-ra), sv[cc * T + tid + j * NT], wk[j]);
-          n1[0] += r.x * r.x + r.y * r.y;
-        }
-      }
-      if (!reduce_ff_arrive<1>(c.g, ss.red, n1)) return false;
-      if (tid < 32) {
-        FF o1[1];
-        reduce_ff_collect<1>(c.g, ss.red, o1);
-        if (tid == 0) {
-          ss.ff_e[k] = make_float2(o1[0].hi, o1[0].lo);
-          ss.ff_e_set |= 1u << k;
-          lzf_finish_step(ss, k, last, o1[0], bd_tol, amax, bmax);
-          if (!ss.stop) {
-            fence_proxy_async_global();  // W_{k+1} of the other CTAs (acquired at the barrier)
-            for (int i = 0; i < ntot && i < kLzStages; ++i) lz_issue(c, wdst, i, gbase + (unsigned)i);
-          }
-        }
-      }
-      __syncthreads();
-    }
-    c.mark(3);
-    vec = wdst;
-    if (ss.stop) break;
   }
   c.lz_count = gbase;
+  c.g.phase = ss.grp.phase;  // the group state goes back to every thread's context
+  c.g.epoch = ss.grp.epoch;
+  c.g.skip_arrival = ss.grp.skip_arrival;
   if (tid < 32) lzf_build_T(ss, m);
   return true;
 }
@@ -1217,12 +1348,13 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
   c.breakdowns = 0;
   c.ring_count = rings[0];
   c.lz_count = rings[1];
-  c.tm = ss.tmem_base + ((((unsigned)threadIdx.x >> 5) & 3u) << 21) + 64u * ((unsigned)threadIdx.x >> 7);
+  c.tm = ss.tmem_base + ((((unsigned)threadIdx.x >> 5) & 3u) << 21) + 128u * ((unsigned)threadIdx.x >> 7);
   c.prof_on = (p.prof != nullptr && rank == 0);
-  c.prof_last = clock64();
-  const long long prof_t0 = c.prof_last;
+  const long long prof_t0 = clock64();
+  if (c.prof_on && threadIdx.x == 0) ss.prof_last = prof_t0;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) c.prof_acc[i] = 0;
+  for (int i = 0; i < 8; ++i)
+    if (c.prof_on && threadIdx.x == 0) ss.prof_acc[i] = 0;
   const bool lead = (rank == 0 && threadIdx.x == 0);
 
   // ---- forward sweep (Alg. "Basic GRAPE", step 4)
@@ -1308,7 +1440,7 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
       p.scal[kScBreakdowns] = (double)c.breakdowns;
       if (c.prof_on) {
         c.mark(6);
-        for (int i = 0; i < 7; ++i) p.prof[i] = c.prof_acc[i];
+        for (int i = 0; i < 7; ++i) p.prof[i] = ss.prof_acc[i];
         p.prof[7] = clock64() - prof_t0;
       }
     }
