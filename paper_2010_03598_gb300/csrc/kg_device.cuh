@@ -92,6 +92,18 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem
                : "memory");
 }
 
+// Asynchronous 16-byte copies global -> shared through L2 only (cp.async.cg), grouped per
+// thread: a thread waits for its own groups, so a thread that reads back only what it copied
+// needs no barrier.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ---------------------------------------------------------------- tensor memory (TMEM)
 // The complex64 resident path keeps thread-private arrays (the tile-leaving part X of H v_k
 // and the own W_k) in tensor memory instead of shared memory: a warp may access the 32 TMEM

@@ -551,6 +551,60 @@ __device__ __forceinline__ void recomb_finalize(const Ctx<V>& c, size_t base, co
 // extra == kExtraOverlapTarget: e = <f|dst> (f = target, complex128, FP64 sums);
 // extra == kExtraGradOverlap:   e.x = Im <dst|Hc|psi_other>.
 // Reads meff, broke and b_m of the Lanczos loop from shared memory.
+// Recombination of the complex64 resident path: basis vectors in flight per thread.
+constexpr int kRecombDepth = 3;  // 3 x 64 KB: all of the resident path's shared memory
+
+// This thread's asynchronous copies of basis vector vk for the own tiles at rb[0..n_own):
+// amplitude pairs 2 (tid + 512 g) + {0, 1}, g < 4, into stage st[(ct * 4 + g) * kThreads + tid].
+__device__ __forceinline__ void recomb_issue(const float2* vk, const size_t (&rb)[2], int n_own, float4* st) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int ct = 0; ct < 2; ++ct) {
+    if (ct < n_own) {
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+        cp_async16(st + (ct * 4 + g) * kThreads + tid, vk + rb[ct] + 2 * (size_t)(tid + g * kThreads));
+    }
+  }
+}
+
+// What the recombination's fused overlaps need, read once per slice.
+struct RecombConsts {
+  const double2* target;
+  unsigned mk;
+  int sx_site;  // Sx control site, or -1 for an Sz-sites control
+  float h_amp;
+};
+
+// One recombined amplitude y at global index gi: store it and add its contributions to
+// ||dst||^2 and to the fused overlap (see recomb_finalize).
+template <class A>
+__device__ __forceinline__ void recomb_amp(const RecombConsts& rc, size_t gi, float2 y, float2* dst, int extra,
+                                           const float2* psi_other, A& nacc, A& gacc, double& ex0, double& ex1) {
+  stv(dst + gi, y);
+  nacc += (A)(y.x * y.x + y.y * y.y);
+  if (extra == kExtraOverlapTarget) {
+    const double2 f = rc.target[gi];
+    ex0 += f.x * (double)y.x + f.y * (double)y.y;
+    ex1 += f.x * (double)y.y - f.y * (double)y.x;
+  } else if (extra == kExtraGradOverlap) {
+    float2 q;
+    if (rc.sx_site >= 0) {
+      q = ldv(psi_other + (gi ^ ((size_t)1 << rc.sx_site)));
+      const float h = 0.5f * rc.h_amp;
+      q.x *= h;
+      q.y *= h;
+    } else {
+      const int nz = __popc(rc.mk) - 2 * __popc((unsigned)gi & rc.mk);
+      const float dz = rc.h_amp * 0.5f * (float)nz;
+      q = ldv(psi_other + gi);
+      q.x *= dz;
+      q.y *= dz;
+    }
+    gacc += (A)(y.x * q.y - y.y * q.x);  // Im(conj(y) q)
+  }
+}
+
 template <class V, class A, int APT, bool WBASIS>
 __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm_src, double tau, V* dst, int extra,
                                              const V* psi_other, double& nrm_dst, double2& e) {
@@ -560,25 +614,20 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
   const int tid = threadIdx.x;
   const int T = c.tile;
   const int meff = ss.meff;
-  // Complex64 resident path: the recombination streams the own tiles of the basis through a
-  // ring of kRingStages 32 KB bulk copies in the shared memory the Lanczos loop no longer
-  // needs; the first copies do not depend on c, so they are issued before the exponential.
-  constexpr int NS = kRingStages;
-  constexpr uint32_t kChunk = 4096u * 8u;  // one tile of one complex64 basis vector
-  auto chunk_src = [&](int i) -> const V* {
-    const int ct = i / meff, k = i - (i / meff) * meff;
-    return ((k == 0) ? src : c.basis_slot(k)) + c.tile_base(ct);
-  };
+  // Complex64 resident path: the recombination streams the own tiles' share of the basis
+  // through the shared memory the Lanczos loop no longer needs, by per-thread asynchronous
+  // copies (cp.async) kRecombDepth basis vectors deep.  Thread tid copies and combines the
+  // amplitude pairs 2 (tid + 512 g) + {0, 1}, g < 4, of each own tile, so it waits only for
+  // its own copies.  The first copies do not depend on c: they go out before the exponential.
+  float4* stg = reinterpret_cast<float4*>(c.sv[0]);  // [kRecombDepth][2 tiles x 4][kThreads]
+  size_t rb[2] = {0, 0};
   if constexpr (WBASIS) {
-    fence_proxy_async();  // earlier generic-proxy writes (basis, psi, ring area) before bulk copies
-    __syncthreads();
-    if (tid == 0) {
-      const int nch = c.n_own * meff;
-      for (int i = 0; i < nch && i < NS; ++i) {
-        const unsigned st = (c.ring_count + (unsigned)i) % NS;
-        mbar_arrive_expect_tx(&ss.mbar[st], kChunk);
-        tma_load_1d(c.sv[0] + (size_t)st * 4096, chunk_src(i), kChunk, &ss.mbar[st]);
-      }
+    rb[0] = (c.n_own > 0) ? c.tile_base(0) : 0;
+    rb[1] = (c.n_own > 1) ? c.tile_base(1) : 0;
+    __syncthreads();  // every thread is done with the Lanczos loop's shared memory
+    for (int s = 0; s < kRecombDepth; ++s) {
+      if (s < meff) recomb_issue(s == 0 ? src : c.basis_slot(s), rb, c.n_own, stg + (size_t)s * 8 * kThreads);
+      cp_async_commit();
     }
   }
   // ---- small exponential and recombination coefficients (warp 0, FP64)
@@ -643,45 +692,50 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
   A nacc = 0, gacc = 0;
   double ex0 = 0.0, ex1 = 0.0;
   if constexpr (WBASIS) {
-    // Complex64 resident path: stream the own tiles of the basis through a 4-stage ring of
-    // 32 KB bulk copies (TMA) in the now idle shared memory; one chunk = one tile of one
-    // basis vector.  Thread 0 issues, every thread waits on the chunk's barrier phase.
-    V* ring = c.sv[0];
-    const int nch = c.n_own * meff;
-    const unsigned g0 = c.ring_count;
-    V y[APT];
+    float4 y[2][4];
 #pragma unroll
-    for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
-    if (meff == 0)  // zero source: the result is zero
-      for (int ct = 0; ct < c.n_own; ++ct)
-        recomb_finalize<V, A, APT>(c, c.tile_base(ct), y, dst, extra, psi_other, nacc, gacc, ex0, ex1);
-    for (int i = 0; i < nch; ++i) {
-      const unsigned g = g0 + (unsigned)i;
-      const unsigned st = g % NS;
-      const bool ok = mbar_wait_bounded(p, &ss.mbar[st], (g / NS) & 1u);
-      const int ct = i / meff, k = i - ct * meff;
-      if (ok) {
-        const R a = (R)ss.coef_re_f[k], b = (R)ss.coef_im_f[k];
-        const V* buf = ring + (size_t)st * 4096;
+    for (int ct = 0; ct < 2; ++ct)
 #pragma unroll
-        for (int j = 0; j < APT; ++j) {
-          const V q = buf[tid + j * kThreads];
-          y[j].x += a * q.x - b * q.y;
-          y[j].y += a * q.y + b * q.x;
-        }
-        if (k == meff - 1) {
-          recomb_finalize<V, A, APT>(c, c.tile_base(ct), y, dst, extra, psi_other, nacc, gacc, ex0, ex1);
+      for (int g = 0; g < 4; ++g) y[ct][g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int n_own = c.n_own;
+    const size_t D = c.D;
+    const float2* slot1 = (const float2*)p.basis;  // basis slot k at slot1 + (k - 1) D
+    for (int k = 0; k < meff; ++k) {
+      cp_async_wait<kRecombDepth - 1>();  // this thread's copies of basis vector k have landed
+      const float a = ss.coef_re_f[k], b = ss.coef_im_f[k];
+      const float4* q = stg + (size_t)(k % kRecombDepth) * 8 * kThreads + tid;
 #pragma unroll
-          for (int j = 0; j < APT; ++j) y[j] = vzero<V>();
+      for (int ct = 0; ct < 2; ++ct) {
+        if (ct < n_own) {
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const float4 w = q[(ct * 4 + g) * kThreads];
+            y[ct][g].x += a * w.x - b * w.y;
+            y[ct][g].y += a * w.y + b * w.x;
+            y[ct][g].z += a * w.z - b * w.w;
+            y[ct][g].w += a * w.w + b * w.z;
+          }
         }
       }
-      if (__syncthreads_or(!ok)) return false;  // every thread is done with stage st
-      if (tid == 0 && i + NS < nch) {
-        mbar_arrive_expect_tx(&ss.mbar[st], kChunk);
-        tma_load_1d(ring + (size_t)st * 4096, chunk_src(i + NS), kChunk, &ss.mbar[st]);
+      if (k + kRecombDepth < meff)
+        recomb_issue(slot1 + (size_t)(k + kRecombDepth - 1) * D, rb, n_own,
+                     stg + (size_t)(k % kRecombDepth) * 8 * kThreads);
+      cp_async_commit();
+    }
+    cp_async_wait<0>();
+    RecombConsts rc;
+    rc.target = reinterpret_cast<const double2*>(p.target);
+    rc.mk = (unsigned)p.hc_mask;
+    rc.sx_site = (p.hc_kind == KG_HC_SX_SITE) ? p.hc_site : -1;
+    rc.h_amp = (float)p.hc_amp;
+    for (int ct = 0; ct < n_own; ++ct) {
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const size_t gi = rb[ct] + 2 * (size_t)(tid + g * kThreads);
+        recomb_amp<A>(rc, gi, make_float2(y[ct][g].x, y[ct][g].y), dst, extra, psi_other, nacc, gacc, ex0, ex1);
+        recomb_amp<A>(rc, gi + 1, make_float2(y[ct][g].z, y[ct][g].w), dst, extra, psi_other, nacc, gacc, ex0, ex1);
       }
     }
-    c.ring_count = g0 + (unsigned)nch;
   } else {
     for (int ct = 0; ct < c.n_own; ++ct) {
       const size_t base = c.tile_base(ct);
