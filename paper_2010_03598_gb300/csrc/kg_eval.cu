@@ -35,7 +35,7 @@ enum ExtraKind { kExtraNone = 0, kExtraOverlapTarget = 1, kExtraGradOverlap = 2 
 constexpr int kLogNT = 9;  // log2(kThreads)
 static_assert((1 << kLogNT) == kThreads, "kLogNT must match kThreads");
 
-constexpr int kRingStages = 6;  // 6 x 32 KB: all of the resident path's shared memory
+constexpr int kSlotRanks = 256;  // groups up to this size prefetch their reduction slots
 constexpr int kLzStages = 4;    // Lanczos partner ring: 4 x 32 KB behind the 64 KB of v_k
 constexpr int kLzMaxChunks = 2 * (1 + (kMaxL - 13) + 1);  // two tiles: bond 11, outer bonds, Sx site
 constexpr uint32_t kTmemCols = 512;  // 128 columns per warp, 4 warps per lane quarter
@@ -67,7 +67,6 @@ struct SmemSlice {
   double s_ap, s_ib, s_bk, s_alpha, s_b2, beta_m, nrm_out, s_ib0;
   float f_ap, f_ib, f_bk, f_alpha, f_ib0, f_bk0, f_beta_m;
   int code1, stop, meff, broke;
-  unsigned long long mbar[kRingStages];  // bulk-copy ring of the recombination (resident complex64 path)
   // resident complex64 path: the Lanczos step's ring of partner-tile copies, its chunk table,
   // the float-float sums of every step (for the FP64 tridiagonal), the TMEM address
   unsigned long long lmbar[kLzStages];
@@ -78,6 +77,7 @@ struct SmemSlice {
   ResCtx r;   // the resident loop's per-slice constants
   Group grp;  // the group's barrier state while the resident loop runs (written by thread 0)
   float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
+  float4 slotbuf[2 * kSlotRanks];  // the group's reduction slots, prefetched by warp 0
   unsigned ff_e_set;
   uint32_t tmem_base;
 };
@@ -201,7 +201,6 @@ struct Ctx {
   unsigned maskL1;  // bonds 0..L-2 in (i ^ i>>1)
   double err_max;
   int breakdowns;
-  unsigned ring_count;   // recombination bulk copies consumed so far (ring stage and phase parity)
   unsigned lz_count;     // Lanczos partner bulk copies consumed so far (complex64 resident path)
   uint32_t tm;           // this warp's TMEM address: its lane quarter, its 128-column group
   bool prof_on;          // phase timing (CTA 0, thread 0; the counters are in shared memory)
@@ -625,9 +624,11 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
     rb[0] = (c.n_own > 0) ? c.tile_base(0) : 0;
     rb[1] = (c.n_own > 1) ? c.tile_base(1) : 0;
     __syncthreads();  // every thread is done with the Lanczos loop's shared memory
-    for (int s = 0; s < kRecombDepth; ++s) {
-      if (s < meff) recomb_issue(s == 0 ? src : c.basis_slot(s), rb, c.n_own, stg + (size_t)s * 8 * kThreads);
-      cp_async_commit();
+    if (tid >= 32) {  // warp 0 issues its copies after the exponential
+      for (int s = 0; s < kRecombDepth; ++s) {
+        if (s < meff) recomb_issue(s == 0 ? src : c.basis_slot(s), rb, c.n_own, stg + (size_t)s * 8 * kThreads);
+        cp_async_commit();
+      }
     }
   }
   // ---- small exponential and recombination coefficients (warp 0, FP64)
@@ -682,6 +683,10 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
         // psi coefficient s_0 / ||psi|| = c_0 - e_1 alpha_0 / ||psi|| (slot 0 held c_0)
         ss.coef_re_f[0] -= er * al * ss.f_ib0;
         ss.coef_im_f[0] -= ei * al * ss.f_ib0;
+      }
+      for (int s = 0; s < kRecombDepth; ++s) {
+        if (s < meff) recomb_issue(s == 0 ? src : c.basis_slot(s), rb, c.n_own, stg + (size_t)s * 8 * kThreads);
+        cp_async_commit();
       }
     }
   }
@@ -957,11 +962,48 @@ __device__ __forceinline__ void lzf_build_T(SmemSlice& ss, int m) {
   __syncwarp();
 }
 
+// Warp 0, right after the barrier that closed a step: asynchronous copies of the group's
+// reduction slots (this step's CTA partials) into shared memory, so that their L2 latency
+// passes while the warp loads partner blocks and runs its stencil.
+__device__ __forceinline__ void slot_prefetch(SmemSlice& ss) {
+  const Group& g = ss.grp;
+  const int size = g.size;
+  if (size <= 1 || size > kSlotRanks) return;
+  const float4* slots = reinterpret_cast<const float4*>(g.red + (size_t)((g.phase - 1) & 1) * g.stride * kNRed);
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < kSlotRanks / 32; ++i) {
+    const int r = lane + 32 * i;
+    if (r < size) {
+      cp_async16(&ss.slotbuf[2 * r], slots + (size_t)r * (kNRed / 2));
+      cp_async16(&ss.slotbuf[2 * r + 1], slots + (size_t)r * (kNRed / 2) + 1);
+    }
+  }
+  cp_async_commit();
+}
+
 // Warp 0 after the barrier that closed step k: float-float totals of the step's sums, then
 // thread 0 sets alpha_k, b_{k+1} and the scalars of step k+1.
 __device__ __forceinline__ void warp0_scalars(SmemSlice& ss, int k, bool last) {
   FF o[3];
-  reduce_ff_collect<3>(ss.grp, ss.red, o);
+  if (ss.grp.size > 1 && ss.grp.size <= kSlotRanks) {
+    // the slots were prefetched into shared memory (slot_prefetch); same summation order as
+    // reduce_ff_collect
+    cp_async_wait<0>();
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    FF t[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int r = lane; r < ss.grp.size; r += 32) {
+      const float4 a = ss.slotbuf[2 * r], b = ss.slotbuf[2 * r + 1];
+      t[0] = ff_add(t[0], FF{a.x, a.y});
+      t[1] = ff_add(t[1], FF{a.z, a.w});
+      t[2] = ff_add(t[2], FF{b.x, b.y});
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) o[v] = ff_warp_sum(t[v]);
+  } else {
+    reduce_ff_collect<3>(ss.grp, ss.red, o);
+  }
   if (threadIdx.x == 0) {
     const FF b2 = lzf_after_reduce(ss, k, last, o);
     if (ss.code1 == 0) lzf_finish_step(ss, k, last, b2, ss.r.bdtol, ss.r.amax, ss.r.bmax);
@@ -1262,12 +1304,18 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
     if (!reduce_ff_arrive_shared<3>(ss.grp, ss.red, acc)) return false;
     if (prof) prof_mark(ss, 2);
     gbase += (unsigned)ring_n(ss);  // every ring copy of step k has been consumed
-    if (!last && tid == 0 && ring_n(ss) > 0) ring_start(ss, wdst, gbase);
+    if (!last && tid < 32) {
+      if (tid == 0 && ring_n(ss) > 0) ring_start(ss, wdst, gbase);
+      slot_prefetch(ss);  // step k's partials, summed by warp 0 during step k+1
+    }
     vec = wdst;
     if (last) done = true;
   }
   if (done) {  // the sums of the last step: alpha_{m-1}, b_m (error indicator)
-    if (tid < 32) warp0_scalars(ss, m - 1, true);
+    if (tid < 32) {
+      slot_prefetch(ss);  // (the last step did not prefetch)
+      warp0_scalars(ss, m - 1, true);
+    }
     __syncthreads();
     if (ss.code1 == 2) {
       if (tid == 0) flag_nonfinite(p);
@@ -1372,7 +1420,7 @@ __device__ __forceinline__ V* fwd_slot(const Ctx<V>& c, int j) {
 // group of `size` CTAs in which this CTA has rank `rank`.  Returns false if the group aborted.
 template <class V, class A, int APT, int TPC, bool RES, bool FAST>
 __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, SmemSlice& ss,
-                                      unsigned char* smem_dyn, unsigned (&rings)[2]) {
+                                      unsigned char* smem_dyn, unsigned& lz_count) {
   Ctx<V> c;
   c.p = &p;
   c.g.rank = rank;
@@ -1400,8 +1448,7 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
   c.maskL1 = (p.L >= 2) ? ((1u << (p.L - 1)) - 1u) : 0u;
   c.err_max = 0.0;
   c.breakdowns = 0;
-  c.ring_count = rings[0];
-  c.lz_count = rings[1];
+  c.lz_count = lz_count;
   c.tm = ss.tmem_base + ((((unsigned)threadIdx.x >> 5) & 3u) << 21) + 128u * ((unsigned)threadIdx.x >> 7);
   c.prof_on = (p.prof != nullptr && rank == 0);
   const long long prof_t0 = clock64();
@@ -1499,8 +1546,7 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
       }
     }
   }
-  rings[0] = c.ring_count;
-  rings[1] = c.lz_count;
+  lz_count = c.lz_count;
   return true;
 }
 
@@ -1508,7 +1554,6 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
 // the tensor memory of the CTA, allocated by warp 0 and freed by it on every way out.
 __device__ __forceinline__ void cta_setup(SmemSlice& ss, bool tmem) {
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kRingStages; ++i) mbar_init(&ss.mbar[i], 1);
     for (int i = 0; i < kLzStages; ++i) mbar_init(&ss.lmbar[i], 1);
     fence_mbar_init();
   }
@@ -1532,8 +1577,8 @@ __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_const
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
   cta_setup(ss, FAST);
-  unsigned rings[2] = {0u, 0u};
-  run_eval<V, A, APT, TPC, RES, FAST>(p, blockIdx.x, gridDim.x, ss, smem_dyn, rings);
+  unsigned lz_count = 0u;  // Lanczos ring copies consumed (stage and phase parity of the ring)
+  run_eval<V, A, APT, TPC, RES, FAST>(p, blockIdx.x, gridDim.x, ss, smem_dyn, lz_count);
   cta_teardown(ss, FAST);
 }
 
@@ -1545,7 +1590,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_batch_kernel(const __grid_cons
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
   cta_setup(ss, true);
-  unsigned rings[2] = {0u, 0u};
+  unsigned lz_count = 0u;  // Lanczos ring copies consumed (stage and phase parity of the ring)
   const int i0 = bp.item_off[blockIdx.x], i1 = bp.item_off[blockIdx.x + 1];
   for (int it = i0; it < i1; ++it) {
     const BatchItem item = bp.items[it];
@@ -1557,11 +1602,11 @@ __global__ void __launch_bounds__(kThreads, 1) kg_batch_kernel(const __grid_cons
     const int ntiles = 1 << (p.L - p.t_bits);
     bool ok;
     if (ntiles <= 2 * item.size && p.t_bits == 12)
-      ok = run_eval<float2, float, 8, 2, true, true>(p, item.rank, item.size, ss, smem_dyn, rings);
+      ok = run_eval<float2, float, 8, 2, true, true>(p, item.rank, item.size, ss, smem_dyn, lz_count);
     else if (ntiles <= 2 * item.size)
-      ok = run_eval<float2, float, 8, 2, true, false>(p, item.rank, item.size, ss, smem_dyn, rings);
+      ok = run_eval<float2, float, 8, 2, true, false>(p, item.rank, item.size, ss, smem_dyn, lz_count);
     else
-      ok = run_eval<float2, float, 8, 1, false, false>(p, item.rank, item.size, ss, smem_dyn, rings);
+      ok = run_eval<float2, float, 8, 1, false, false>(p, item.rank, item.size, ss, smem_dyn, lz_count);
     if (!ok) break;
     __syncthreads();
   }
