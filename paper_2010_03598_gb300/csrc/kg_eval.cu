@@ -33,10 +33,19 @@ namespace kg {
 enum ExtraKind { kExtraNone = 0, kExtraOverlapTarget = 1, kExtraGradOverlap = 2 };
 
 constexpr int kLogNT = 9;  // log2(kThreads)
+// Lanczos loop of a kernel: generic (any tile, complex64 or complex128), complex64 resident
+// (4096-amplitude tiles, two per CTA, on chip), complex64 streaming (4096-amplitude tiles
+// that do not stay on chip).
+enum { kModeGeneric = 0, kModeResident64 = 1, kModeStream64 = 2 };
 static_assert((1 << kLogNT) == kThreads, "kLogNT must match kThreads");
 
 constexpr int kSlotRanks = 256;  // groups up to this size prefetch their reduction slots
-constexpr int kLzStages = 4;    // Lanczos partner ring: 4 x 32 KB behind the 64 KB of v_k
+constexpr int kLzStages = 4;
+// complex64 streaming path: per-thread copy ring of kStrDepth blocks (4 granules of 16 B per
+// thread each) behind two tiles of v_k for the stencil
+constexpr int kStrDepth = 4;
+constexpr int kStrSvBufs = 2;  // tiles of v_k for the stencil (1: one more barrier per tile)
+constexpr size_t kStrSmemBytes = (size_t)kStrSvBufs * 4096 * 8 + (size_t)kStrDepth * 4 * 512 * 16;    // Lanczos partner ring: 4 x 32 KB behind the 64 KB of v_k
 constexpr int kLzMaxChunks = 2 * (1 + (kMaxL - 13) + 1);  // two tiles: bond 11, outer bonds, Sx site
 constexpr uint32_t kTmemCols = 512;  // 128 columns per warp, 4 warps per lane quarter
 
@@ -195,7 +204,7 @@ struct Ctx {
   V* sv[2];         // shared memory: v_k and v_{k-1} of the own tiles ([TPC][tile] each)
   V* sx;            // shared memory (resident variant): X of the own tiles ([TPC][tile])
   int t, tile, ntiles, n_own;
-  bool paired;      // size == ntiles/2: CTA r owns tiles 2r and 2r ^ alt (equal cross-tile work)
+  bool paired;      // tiles go to CTAs in pairs (2p, 2p ^ alt), pair p to CTA p mod size (equal cross-tile work)
   unsigned alt;     // alternating bits 0, 2, 4, ... of the tile index
   size_t D;
   unsigned maskL1;  // bonds 0..L-2 in (i ^ i>>1)
@@ -215,8 +224,8 @@ struct Ctx {
   // same number of tile-uniform antiparallel bonds (cross-tile partner tiles) as any other pair.
   __device__ size_t tile_base(int c) const {
     if (paired) {
-      const unsigned T0 = 2u * (unsigned)g.rank;
-      return (size_t)(c == 0 ? T0 : (T0 ^ alt)) << t;
+      const unsigned T0 = 2u * (unsigned)(g.rank + (c >> 1) * g.size);
+      return (size_t)((c & 1) ? (T0 ^ alt) : T0) << t;
     }
     return (size_t)(g.rank + c * g.size) << t;
   }
@@ -1330,16 +1339,357 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
   return true;
 }
 
+// ---------------------------------------------------------------- complex64 streaming path
+// For chains whose tiles do not stay on chip (more than two 4096-amplitude tiles per CTA), every
+// Lanczos step streams each own tile through the SM.  Same recurrence and global layout as
+// lanczos_generic (basis of normalised v_k, W ping-pong, X scratch), but a thread owns amplitude
+// PAIRS 2q, 2q+1 with q = tid + 512 g, g < 4, so that every block it needs -- its own W_k, X_{k-1},
+// v_{k-1} and, element for element, the partner blocks of W_k -- arrives by 16-byte asynchronous
+// copies (cp.async.cg) of exactly the granules it will read.  The copies run kStrDepth blocks
+// ahead through a per-thread ring in shared memory: no block barrier, no registers held, and no
+// single copy engine to queue behind.  Only the stencil's neighbour reads need one barrier per tile.
+
+// One block of a tile's stream: granule g of the own tile (bit g of gmask) reads granule g ^ gx
+// of the source tile starting at `src`.
+struct StrBlk {
+  const float2* src;
+  unsigned gmask;
+  int gx;
+};
+
+// Partner blocks of the tile at `base` (for W = vector w): bond 11 (own half h = 1 - bt against
+// half bt of tile base ^ 2^12: granules g with bit 1 = h, source granule g ^ 2), the antiparallel
+// bonds b >= 12 (tile base ^ (3 << b)), an Sx control on a site >= 12 (tile base ^ (1 << s),
+// weight of the control).  str_partners returns their number; str_partner the n-th of them.
+__device__ __forceinline__ unsigned str_outer(size_t base, int L1) {
+  unsigned act = 0;
+  for (int b = 12; b < L1; ++b)
+    if (((base >> b) ^ (base >> (b + 1))) & 1u) act |= 1u << (b - 12);
+  return act;
+}
+__device__ __forceinline__ int str_partners(size_t base, int L1, bool sx12) {
+  return ((L1 > 11) ? 1 : 0) + __popc(str_outer(base, L1)) + (sx12 ? 1 : 0);
+}
+__device__ __forceinline__ StrBlk str_partner(size_t base, const float2* w, int L1, int hs, bool sx12, int n,
+                                              bool& is_ctrl) {
+  is_ctrl = false;
+  if (L1 > 11) {
+    if (n == 0) {
+      const unsigned h = 1u - (unsigned)((base >> 12) & 1u);
+      return {w + (base ^ ((size_t)1 << 12)), h ? 0xcu : 0x3u, 2};
+    }
+    --n;
+  }
+  unsigned act = str_outer(base, L1);
+  const int na = __popc(act);
+  if (n < na) {
+    for (int i = 0; i < n; ++i) act &= act - 1;
+    const int b = 12 + __ffs(act) - 1;
+    return {w + (base ^ ((size_t)3 << b)), 0xfu, 0};
+  }
+  is_ctrl = sx12;
+  return {w + (base ^ ((size_t)1 << hs)), 0xfu, 0};
+}
+
+// This thread's copies of block `bk` into ring stage st: stage layout [kStrDepth][4][512] float4.
+__device__ __forceinline__ void str_issue(float4* ring, int st, const StrBlk& bk) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+    if ((bk.gmask >> g) & 1u)
+      cp_async16(ring + (st * 4 + g) * kThreads + tid, bk.src + 2 * (size_t)(tid + ((g ^ bk.gx) << 9)));
+}
+
+// The stream of one step: for every own tile c (in order) its partner blocks, then X_{k-1}
+// and v_{k-1} (k > 0), then W_k.  StrCursor walks it; both the issuer (kStrDepth blocks ahead)
+// and the consumer use one, all threads identically.
+struct StrStep {
+  const float2* w;      // W_k (all tiles)
+  const float2* x;      // X_{k-1}
+  const float2* vprev;  // v_{k-1} (k = 1: psi, scaled on use)
+  int k, L1, hs, n_own;
+  bool sx12;
+};
+struct StrCursor {
+  int c, b, nb;  // tile, block within the tile, blocks of the tile
+  size_t base;
+};
+__device__ __forceinline__ int str_nblk(const StrStep& S, size_t base) {
+  return str_partners(base, S.L1, S.sx12) + (S.k > 0 ? 3 : 1);
+}
+__device__ __forceinline__ void str_cursor_tile(const Ctx<float2>& c, const StrStep& S, StrCursor& u) {
+  if (u.c < S.n_own) {
+    u.base = c.tile_base(u.c);
+    u.nb = str_nblk(S, u.base);
+  }
+}
+// Block b of the tile at `base`: partners first, then (k > 0) X and V, then W.
+__device__ __forceinline__ StrBlk str_block(const StrStep& S, size_t base, int b) {
+  const int np = str_partners(base, S.L1, S.sx12);
+  if (b < np) {
+    bool ctrl;
+    return str_partner(base, S.w, S.L1, S.hs, S.sx12, b, ctrl);
+  }
+  b -= np;
+  if (S.k == 0) return {S.w + base, 0xfu, 0};
+  if (b == 0) return {S.x + base, 0xfu, 0};
+  if (b == 1) return {S.vprev + base, 0xfu, 0};
+  return {S.w + base, 0xfu, 0};
+}
+// Issuer: copy the block under the cursor (if the step has one left) and advance; one commit
+// group per call, empty past the end, so that every consumed block is exactly kStrDepth - 1
+// groups behind the newest.
+__device__ __forceinline__ void str_issue_next(const Ctx<float2>& c, const StrStep& S, StrCursor& u, float4* ring,
+                                               int& slot) {
+  if (u.c < S.n_own) {
+    str_issue(ring, slot, str_block(S, u.base, u.b));
+    if (++u.b == u.nb) {
+      ++u.c;
+      u.b = 0;
+      str_cursor_tile(c, S, u);
+    }
+  }
+  cp_async_commit();
+  slot = (slot + 1 == kStrDepth) ? 0 : slot + 1;
+}
+
+__device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 f4add(float4 x, float4 y) {
+  return make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+}
+__device__ __forceinline__ float4 f4scale(float a, float4 x) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
+__device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// Consume the next ring stage: wait until this thread's copies of it have landed.
+__device__ __forceinline__ const float4* str_wait(const float4* ring, int slot) {
+  cp_async_wait<kStrDepth - 1>();
+  return ring + slot * 4 * kThreads + threadIdx.x;
+}
+
+// Complex64 streaming Lanczos loop of one slice (see above).  Scalars, reductions and the
+// breakdown handling are those of lanczos_generic.
+__device__ __noinline__ bool lanczos_str64(Ctx<float2>& c, const float2* src, double nrm_src, double uj) {
+  const EvalParams& p = *c.p;
+  SmemSlice& ss = *c.ss;
+  constexpr int NT = kThreads;
+  const int m = p.m;
+  const int tid = threadIdx.x;
+  const float hxy = (float)(0.5 * p.Jxy), qz = (float)(0.25 * p.Jz);
+  const float cu_sx = (float)(0.5 * uj * p.hc_amp), cu_sz = (float)(uj * p.hc_amp);
+  const unsigned mk = (unsigned)p.hc_mask;
+  const bool hc_sx = (p.hc_kind == KG_HC_SX_SITE);
+  const int hs = p.hc_site, L1 = p.L - 1;
+  const unsigned maskL1 = c.maskL1;
+  const size_t D = c.D;
+  float4* sv4 = reinterpret_cast<float4*>(c.sv[0]);  // [kStrSvBufs][2048] pairs: v_k of the tile in hand
+  float4* ring = sv4 + kStrSvBufs * 2048;            // [kStrDepth][4][512] per-thread copy ring
+  float2* basis = (float2*)p.basis;                  // slot k at basis + (k - 1) D
+  float2* wb = (float2*)p.wbuf;
+  float2* xb = (float2*)p.xbuf;
+  double amax = 0.0, bmax = 0.0;  // thread 0: running maxima for the breakdown test
+  if (tid == 0) lz_init(ss, nrm_src, m);
+  __syncthreads();
+  if (ss.meff == 0) return true;
+  StrStep S;
+  S.L1 = L1;
+  S.hs = hs;
+  S.n_own = c.n_own;
+  S.sx12 = hc_sx && hs >= 12;
+  for (int k = 0; k < m; ++k) {
+    const bool last = (k == m - 1);
+    S.k = k;
+    S.w = (k == 0) ? src : wb + (size_t)(k & 1) * D;
+    S.x = xb;
+    S.vprev = (k <= 1) ? src : basis + (size_t)(k - 2) * D;
+    float2* vslot = (k == 0) ? nullptr : basis + (size_t)(k - 1) * D;  // v_k
+    float2* wdst = last ? nullptr : wb + (size_t)((k + 1) & 1) * D;    // W_{k+1}
+    const float ap = ss.f_ap, ib = ss.f_ib, bk = ss.f_bk;
+    const float vsc = (k == 1) ? ss.f_ib0 : 1.f;  // slot 0 is psi itself: v_0 = psi / b_0
+    StrCursor iu{0, 0, 0, 0};
+    str_cursor_tile(c, S, iu);
+    int islot = 0, cslot = 0;
+    for (int d = 0; d < kStrDepth; ++d) str_issue_next(c, S, iu, ring, islot);
+    float acc_a = 0.f, acc_n = 0.f, acc_q = 0.f;
+    for (int ct = 0; ct < S.n_own; ++ct) {
+      const size_t base = c.tile_base(ct);
+      const int np = str_partners(base, L1, S.sx12);
+      // ---- partner sums of W_k, block by block
+      float4 xs[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) xs[g] = f4zero();
+      for (int b = 0; b < np; ++b) {
+        bool ctrl;
+        const StrBlk blk = str_partner(base, S.w, L1, hs, S.sx12, b, ctrl);
+        const float wg = ctrl ? cu_sx : hxy;
+        const float4* q = str_wait(ring, cslot);
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+          if ((blk.gmask >> g) & 1u) xs[g] = f4fma(wg, q[g * NT], xs[g]);
+        str_issue_next(c, S, iu, ring, islot);
+        cslot = (cslot + 1 == kStrDepth) ? 0 : cslot + 1;
+      }
+      // ---- own blocks, each folded in as it arrives: X_{k-1} (X_k = (XS_k - alpha X_{k-1}) / b_k),
+      //      v_{k-1}, W_k (v_k = (W_k - alpha v_{k-1}) / b_k; x <- X_k - b_k v_{k-1}, the part of
+      //      W_{k+1} that needs no neighbour)
+      float4* sv = sv4 + (ct % kStrSvBufs) * 2048;
+      float4 x[4], vp[4];
+      if (k > 0) {
+        const float4* q = str_wait(ring, cslot);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) x[g] = f4scale(ib, f4fma(-ap, q[g * NT], xs[g]));
+        str_issue_next(c, S, iu, ring, islot);
+        cslot = (cslot + 1 == kStrDepth) ? 0 : cslot + 1;
+        q = str_wait(ring, cslot);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) vp[g] = f4scale(vsc, q[g * NT]);
+        str_issue_next(c, S, iu, ring, islot);
+        cslot = (cslot + 1 == kStrDepth) ? 0 : cslot + 1;
+      } else {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) x[g] = f4scale(ib, xs[g]);
+      }
+      if (kStrSvBufs == 1) __syncthreads();  // the previous tile's stencil is done with sv
+      {
+        const float4* q = str_wait(ring, cslot);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int qi = tid + g * NT;
+          const float4 w = q[g * NT];
+          float4 v;
+          if (k == 0) {
+            v = f4scale(ib, w);
+          } else {
+            v = f4scale(ib, f4fma(-ap, vp[g], w));
+            __stcg(reinterpret_cast<float4*>(vslot + base) + qi, v);
+          }
+          sv[qi] = v;
+          if (!last) __stcg(reinterpret_cast<float4*>(xb + base) + qi, x[g]);
+          if (k > 0) x[g] = f4fma(-bk, vp[g], x[g]);
+        }
+        str_issue_next(c, S, iu, ring, islot);
+        cslot = (cslot + 1 == kStrDepth) ? 0 : cslot + 1;
+      }
+      __syncthreads();  // the tile's v_k is complete in shared memory
+      float4 vv[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) vv[g] = sv[tid + g * NT];
+      // ---- stage 2: W_{k+1} = H v_k - b_k v_{k-1} (the latter already in x), partial sums
+      float4 h[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) h[g] = f4zero();
+      {  // bond 0: bits 0 (pair element) and 1 (bit 0 of tid); partner pair of tid ^ 1, swapped
+        const bool q0 = (tid & 1) != 0;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const float4 Q = sv[(tid ^ 1) + g * NT];
+          if (!q0) {
+            h[g].z += Q.x;
+            h[g].w += Q.y;
+          } else {
+            h[g].x += Q.z;
+            h[g].y += Q.w;
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 1; b <= 8; ++b) {  // bonds 1..8: bits b-1, b of tid
+        if (((tid >> (b - 1)) ^ (tid >> b)) & 1) {
+#pragma unroll
+          for (int g = 0; g < 4; ++g) h[g] = f4add(h[g], sv[(tid ^ (3 << (b - 1))) + g * NT]);
+        }
+      }
+      {  // bond 9: bit 8 of tid, bit 0 of g
+        const int t8 = (tid >> 8) & 1;
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+          if (t8 != (g & 1)) h[g] = f4add(h[g], sv[(tid ^ 256) + (g ^ 1) * NT]);
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g)  // bond 10: bits 0, 1 of g
+        if ((g ^ (g >> 1)) & 1) h[g] = f4add(h[g], vv[g ^ 3]);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int q = tid + g * NT;
+        float4 cx = f4zero();  // in-tile Sx control partner of each element
+        if (hc_sx && hs < 12) {
+          if (hs == 0) {
+            cx = make_float4(vv[g].z, vv[g].w, vv[g].x, vv[g].y);
+          } else {
+            cx = sv[q ^ (1 << (hs - 1))];
+          }
+        }
+        float d[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const unsigned gi = (unsigned)(base + 2 * (size_t)q + e);
+          const unsigned xg = (gi ^ (gi >> 1)) & maskL1;
+          d[e] = qz * (float)(L1 - 2 * __popc(xg));
+          if (!hc_sx) d[e] += cu_sz * 0.5f * (float)(__popc(mk) - 2 * __popc(gi & mk));
+        }
+        float4 wn;
+        wn.x = d[0] * vv[g].x + hxy * h[g].x + x[g].x + cu_sx * cx.x;
+        wn.y = d[0] * vv[g].y + hxy * h[g].y + x[g].y + cu_sx * cx.y;
+        wn.z = d[1] * vv[g].z + hxy * h[g].z + x[g].z + cu_sx * cx.z;
+        wn.w = d[1] * vv[g].w + hxy * h[g].w + x[g].w + cu_sx * cx.w;
+        acc_a += vv[g].x * wn.x + vv[g].y * wn.y + vv[g].z * wn.z + vv[g].w * wn.w;
+        acc_n += wn.x * wn.x + wn.y * wn.y + wn.z * wn.z + wn.w * wn.w;
+        acc_q += vv[g].x * vv[g].x + vv[g].y * vv[g].y + vv[g].z * vv[g].z + vv[g].w * vv[g].w;
+        if (!last) __stcg(reinterpret_cast<float4*>(wdst + base) + q, wn);
+      }
+    }
+    c.mark(0);
+    float acc[3] = {acc_a, acc_n, acc_q};
+    double out[3];
+    if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
+    c.mark(2);
+    if (tid == 0) lz_after_reduce(ss, k, last, out);
+    __syncthreads();
+    const int code = ss.code1;
+    if (code == 2) {
+      if (tid == 0) flag_nonfinite(p);
+      return false;
+    }
+    if (code == 1) {
+      // near an invariant subspace: ||W_{k+1} - alpha_k v_k||^2 explicitly (one more reduction)
+      float n1[1] = {0.f};
+      const float ra = ss.f_alpha;
+      for (int ct = 0; ct < S.n_own; ++ct) {
+        const size_t base = c.tile_base(ct);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int q = tid + g * NT;
+          const float4 wn = __ldcg(reinterpret_cast<const float4*>(wdst + base) + q);
+          const float4 v = (k == 0) ? f4scale(ib, __ldcg(reinterpret_cast<const float4*>(src + base) + q))
+                                    : __ldcg(reinterpret_cast<const float4*>(vslot + base) + q);
+          const float4 r = f4fma(-ra, v, wn);
+          n1[0] += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+        }
+      }
+      double o1[1];
+      if (!group_reduce<1>(c.g, ss.red, n1, o1)) return false;
+      if (tid == 0) ss.s_b2 = o1[0];
+    }
+    if (tid == 0) lz_finish_step(ss, k, last, p.bd_tol, amax, bmax);
+    __syncthreads();
+    c.mark(3);
+    if (ss.stop) break;
+  }
+  return true;
+}
+
 // One Krylov step src -> dst (App. A): Lanczos basis, small exponential, recombination.
 // tau = sigma * dt.  Returns false on abort.
-template <class V, class A, int APT, int TPC, bool RES, bool FAST>
+template <class V, class A, int APT, int TPC, bool RES, int MODE>
 __device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_src, double uj, double tau, V* dst,
                                           int extra, const V* psi_other, double& nrm_dst, double2& e) {
   bool ok;
-  if constexpr (FAST) ok = lanczos_res64(c, src, nrm_src, uj);
+  if constexpr (MODE == kModeResident64) ok = lanczos_res64(c, src, nrm_src, uj);
+  else if constexpr (MODE == kModeStream64) ok = lanczos_str64(c, src, nrm_src, uj);
   else ok = lanczos_generic<V, A, APT, TPC, RES>(c, src, nrm_src, uj);
   if (!ok) return false;
-  return finish_slice<V, A, APT, FAST>(c, src, nrm_src, tau, dst, extra, psi_other, nrm_dst, e);
+  return finish_slice<V, A, APT, MODE == kModeResident64>(c, src, nrm_src, tau, dst, extra, psi_other, nrm_dst, e);
 }
 
 // chi_N = beta f, ||chi_N||, and G_N = 2 dt Im <chi_N|Hc|psi_N>.
@@ -1418,7 +1768,7 @@ __device__ __forceinline__ V* fwd_slot(const Ctx<V>& c, int j) {
 
 // One whole evaluation (forward sweep, overlap, co-state sweep, gradient) of problem p by the
 // group of `size` CTAs in which this CTA has rank `rank`.  Returns false if the group aborted.
-template <class V, class A, int APT, int TPC, bool RES, bool FAST>
+template <class V, class A, int APT, int TPC, bool RES, int MODE>
 __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, SmemSlice& ss,
                                       unsigned char* smem_dyn, unsigned& lz_count) {
   Ctx<V> c;
@@ -1442,8 +1792,15 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
   c.sx = c.sv[1] + (size_t)NB * c.tile;
   c.D = (size_t)1 << p.L;
   c.ntiles = (int)(c.D >> p.t_bits);
-  c.n_own = (c.ntiles - c.g.rank + c.g.size - 1) / c.g.size;
-  c.paired = (c.ntiles >= 2 && 2 * c.g.size == c.ntiles);
+  // Pairs (resident paths with two tiles per CTA, and the complex64 streaming path): every pair
+  // has the same number of cross-tile partner blocks, so dealing pairs balances the CTAs.
+  c.paired = (c.ntiles >= 2 && (2 * c.g.size == c.ntiles || MODE == kModeStream64));
+  if (c.paired) {
+    const int npairs = c.ntiles / 2;
+    c.n_own = (c.g.rank < npairs) ? 2 * ((npairs - c.g.rank + c.g.size - 1) / c.g.size) : 0;
+  } else {
+    c.n_own = (c.ntiles - c.g.rank + c.g.size - 1) / c.g.size;
+  }
   c.alt = 0x55555555u & (unsigned)(c.ntiles - 1);
   c.maskL1 = (p.L >= 2) ? ((1u << (p.L - 1)) - 1u) : 0u;
   c.err_max = 0.0;
@@ -1468,7 +1825,7 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
     double nrm_new;
     double2 e;
     const int extra = (j == p.N) ? kExtraOverlapTarget : kExtraNone;
-    if (!krylov_slice<V, A, APT, TPC, RES, FAST>(c, fwd_slot<V>(c, j - 1), nrm_prev, p.u[j - 1], p.dt, fwd_slot<V>(c, j),
+    if (!krylov_slice<V, A, APT, TPC, RES, MODE>(c, fwd_slot<V>(c, j - 1), nrm_prev, p.u[j - 1], p.dt, fwd_slot<V>(c, j),
                                            extra, nullptr, nrm_new, e))
       return false;
     if (lead) p.nrm[j] = nrm_new;
@@ -1504,7 +1861,7 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
           V* d = (V*)p.seg + (size_t)(i - a - 1) * c.D;
           double nn;
           double2 e;
-          if (!krylov_slice<V, A, APT, TPC, RES, FAST>(c, prev, np, p.u[i - 1], p.dt, d, kExtraNone, nullptr, nn, e))
+          if (!krylov_slice<V, A, APT, TPC, RES, MODE>(c, prev, np, p.u[i - 1], p.dt, d, kExtraNone, nullptr, nn, e))
             return false;
           prev = d;
           np = nn;
@@ -1517,7 +1874,7 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
         else psi_jm1 = (V*)p.seg + (size_t)(j - 1 - a - 1) * c.D;
         double nn;
         double2 e;
-        if (!krylov_slice<V, A, APT, TPC, RES, FAST>(c, chi[cur], nchi, p.u[j - 1], -p.dt, chi[cur ^ 1],
+        if (!krylov_slice<V, A, APT, TPC, RES, MODE>(c, chi[cur], nchi, p.u[j - 1], -p.dt, chi[cur ^ 1],
                                                kExtraGradOverlap, psi_jm1, nn, e))
           return false;
         if (lead) p.G[j - 1] = 2.0 * p.dt * e.x;
@@ -1572,14 +1929,14 @@ __device__ __forceinline__ void cta_teardown(SmemSlice& ss, bool tmem) {
   if (threadIdx.x < 32) tmem_dealloc(ss.tmem_base, kTmemCols);
 }
 
-template <class V, class A, int APT, int TPC, bool RES, bool FAST>
+template <class V, class A, int APT, int TPC, bool RES, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_constant__ EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
-  cta_setup(ss, FAST);
+  cta_setup(ss, MODE == kModeResident64);
   unsigned lz_count = 0u;  // Lanczos ring copies consumed (stage and phase parity of the ring)
-  run_eval<V, A, APT, TPC, RES, FAST>(p, blockIdx.x, gridDim.x, ss, smem_dyn, lz_count);
-  cta_teardown(ss, FAST);
+  run_eval<V, A, APT, TPC, RES, MODE>(p, blockIdx.x, gridDim.x, ss, smem_dyn, lz_count);
+  cta_teardown(ss, MODE == kModeResident64);
 }
 
 // Many independent problems (complex64) in one cooperative launch.  Every CTA walks its own
@@ -1602,11 +1959,11 @@ __global__ void __launch_bounds__(kThreads, 1) kg_batch_kernel(const __grid_cons
     const int ntiles = 1 << (p.L - p.t_bits);
     bool ok;
     if (ntiles <= 2 * item.size && p.t_bits == 12)
-      ok = run_eval<float2, float, 8, 2, true, true>(p, item.rank, item.size, ss, smem_dyn, lz_count);
+      ok = run_eval<float2, float, 8, 2, true, kModeResident64>(p, item.rank, item.size, ss, smem_dyn, lz_count);
     else if (ntiles <= 2 * item.size)
-      ok = run_eval<float2, float, 8, 2, true, false>(p, item.rank, item.size, ss, smem_dyn, lz_count);
+      ok = run_eval<float2, float, 8, 2, true, kModeGeneric>(p, item.rank, item.size, ss, smem_dyn, lz_count);
     else
-      ok = run_eval<float2, float, 8, 1, false, false>(p, item.rank, item.size, ss, smem_dyn, lz_count);
+      ok = run_eval<float2, float, 8, 1, false, kModeGeneric>(p, item.rank, item.size, ss, smem_dyn, lz_count);
     if (!ok) break;
     __syncthreads();
   }
@@ -1652,21 +2009,25 @@ struct KernelChoice {
   size_t smem;
 };
 
-template <class V, class A, int APT, int TPC, bool RES, bool FAST>
+template <class V, class A, int APT, int TPC, bool RES, int MODE>
 static KernelChoice choice(int t_bits) {
   constexpr int NB = RES ? TPC : 1;
-  return {(const void*)kg_eval_kernel<V, A, APT, TPC, RES, FAST>,
-          (size_t)(RES ? 3 : 2) * NB * ((size_t)1 << t_bits) * sizeof(V)};
+  // complex64 streaming: two v_k tiles for the stencil plus the per-thread copy ring
+  const size_t smem = (MODE == kModeStream64) ? kStrSmemBytes
+                                              : (size_t)(RES ? 3 : 2) * NB * ((size_t)1 << t_bits) * sizeof(V);
+  return {(const void*)kg_eval_kernel<V, A, APT, TPC, RES, MODE>, smem};
 }
 
 // Variants: complex64 resident with full 4096-amplitude tiles (specialised loop), complex64
-// resident (<= 2 tiles of <= 4096 amplitudes per CTA), complex64 streaming, complex128
-// streaming (tiles of <= 2048 amplitudes).
+// resident (<= 2 tiles of <= 4096 amplitudes per CTA), complex64 streaming (specialised loop
+// for 4096-amplitude tiles, generic otherwise), complex128 streaming (tiles of <= 2048
+// amplitudes).
 static KernelChoice pick(int prec, int variant, int t_bits) {
-  if (prec == KG_PREC_C128) return choice<double2, double, 4, 1, false, false>(t_bits);
-  if (variant == kVariantResidentFull) return choice<float2, float, 8, 2, true, true>(t_bits);
-  if (variant == kVariantResident) return choice<float2, float, 8, 2, true, false>(t_bits);
-  return choice<float2, float, 8, 1, false, false>(t_bits);
+  if (prec == KG_PREC_C128) return choice<double2, double, 4, 1, false, kModeGeneric>(t_bits);
+  if (variant == kVariantResidentFull) return choice<float2, float, 8, 2, true, kModeResident64>(t_bits);
+  if (variant == kVariantResident) return choice<float2, float, 8, 2, true, kModeGeneric>(t_bits);
+  if (t_bits == 12) return choice<float2, float, 8, 1, false, kModeStream64>(t_bits);
+  return choice<float2, float, 8, 1, false, kModeGeneric>(t_bits);
 }
 
 int max_tile_bits(int prec) { return prec == KG_PREC_C128 ? kLogNT + 2 : kLogNT + 3; }

@@ -110,6 +110,33 @@ def test_multi_cta_tilings_vs_oracle(tile_bits, ctas):
         check(prec, F, g, F_ref, g_ref)
 
 
+@pytest.mark.parametrize("L,ctas,hc", [(14, 1, ("sx", 0)), (15, 3, ("sx", 13)), (16, 5, ("sz", None)),
+                                        (15, 2, ("sx", 5))])
+def test_streaming_complex64_tiles_vs_oracle(L, ctas, hc):
+    # 4096-amplitude tiles, more than two per CTA (ragged: 4 pairs of tiles on 3 CTAs, 8 on 5):
+    # the complex64 streaming loop, with the Sx control inside a tile, above the tile bits, and
+    # the paper's Sz edge control.
+    N, m, dt = 5, 12, 0.05
+    rng = np.random.default_rng(300 + L + ctas)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    kind, site = hc
+    if kind == "sx":
+        ch = oracle.Chain(L, 1.0, 0.6, "sx", hc_site=site, hc_amp=0.8)
+        spec = dict(hc_kind="sx", hc_site=site, hc_amp=0.8)
+    else:
+        mask = 1 | (1 << (L - 1))
+        ch = oracle.Chain(L, 1.0, 0.6, "sz", hc_mask=mask, hc_amp=1.0)
+        spec = dict(hc_kind="sz", hc_mask=mask, hc_amp=1.0)
+    F_ref, g_ref, _ = oracle.evaluate(ch, u, dt, m, psi0, f, "centered")
+    A = api()
+    F, g, rep = run_gpu(A.ChainSpec(L, 1.0, 0.6, **spec), A.Options(N, dt, m, prec="c64", tile_bits=12, ctas=ctas),
+                        u, psi0, f)
+    assert rep["tile_bits"] == 12 and 2 * rep["ctas"] < (1 << (L - 12))  # streaming, not resident
+    check("c64", F, g, F_ref, g_ref)
+
+
 @pytest.mark.parametrize("site", [0, 4, 8])
 def test_sx_control_on_other_sites(site):
     L, N, m = 9, 6, 12
