@@ -100,6 +100,12 @@ typedef struct kg_options {
 
 #define KG_FLAG_HOST_STAGING 1u  /* reserve workspace for kg_evaluate_host's input/output copies */
 #define KG_FLAG_PHASE_TIMING 2u  /* record per-phase SM cycles of CTA 0 into kg_report.phase_cycles */
+/* Full re-orthogonalisation (App. A names it as the remedy for the loss of orthogonality of the
+ * Lanczos vectors): after each step, classical Gram-Schmidt of the residual against every basis
+ * vector, applied twice; b_{k+1} is the norm of what remains.  Without the flag the recurrence
+ * removes only the last two directions, as in Alg. "Lanczos".  Runs the generic streaming
+ * kernel (two more passes over the basis per step), for any precision. */
+#define KG_FLAG_FULL_REORTH 4u
 
 /* Diagnostics of the last evaluation, filled by kg_sync. */
 typedef struct kg_report {

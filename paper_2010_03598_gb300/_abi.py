@@ -15,6 +15,7 @@ KG_GRAD_NONE, KG_GRAD_CENTERED, KG_GRAD_ZEROTH = 0, 1, 2
 KG_HC_SX_SITE, KG_HC_SZ_SITES = 0, 1
 KG_FLAG_HOST_STAGING = 1
 KG_FLAG_PHASE_TIMING = 2
+KG_FLAG_FULL_REORTH = 4
 KG_STATIC_WORKSPACE_BYTES = 64 << 20
 
 

@@ -49,10 +49,12 @@ class Options:
     host_staging: bool = False
     phase_timing: bool = False
     breakdown_tol: float = 0.0
+    reorth: bool = False      # full Gram-Schmidt (twice) against the whole Krylov basis every step
 
     def to_c(self) -> _abi.KgOptions:
         flags = (_abi.KG_FLAG_HOST_STAGING if self.host_staging else 0) | \
-            (_abi.KG_FLAG_PHASE_TIMING if self.phase_timing else 0)
+            (_abi.KG_FLAG_PHASE_TIMING if self.phase_timing else 0) | \
+            (_abi.KG_FLAG_FULL_REORTH if self.reorth else 0)
         return _abi.KgOptions(self.N, self.m, _PREC[self.prec], _GRAD[self.grad], self.ckpt_every, self.tile_bits,
                               self.ctas, flags, self.dt, self.breakdown_tol)
 

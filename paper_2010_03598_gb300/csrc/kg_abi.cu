@@ -63,7 +63,7 @@ kg_status check_args(const kg_chain* ch, const kg_options* o) {
   if (o->tile_bits != 0 && (o->tile_bits < 1 || o->tile_bits > 13))
     return fail(KG_ERR_INVALID_ARG, "tile_bits must be 0 (auto) or 1..13");
   if (o->ctas < 0 || o->ctas > kg::kMaxCtas) return fail(KG_ERR_INVALID_ARG, "ctas must be 0 (auto) or 1..2048");
-  if ((o->flags & ~(KG_FLAG_HOST_STAGING | KG_FLAG_PHASE_TIMING)) != 0)
+  if ((o->flags & ~(KG_FLAG_HOST_STAGING | KG_FLAG_PHASE_TIMING | KG_FLAG_FULL_REORTH)) != 0)
     return fail(KG_ERR_INVALID_ARG, "unknown flag bits");
   if (!(o->dt > 0.0) || !std::isfinite(o->dt)) return fail(KG_ERR_INVALID_ARG, "dt must be finite and > 0");
   if (std::isnan(o->breakdown_tol)) return fail(KG_ERR_INVALID_ARG, "breakdown_tol must not be NaN");
@@ -178,7 +178,7 @@ kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options*
   int variant = kg::kVariantStreaming;
   int ctas = 0;
   const int tpc = kg::resident_tiles_per_cta(opts->prec);
-  if (tpc > 0) {
+  if (tpc > 0 && !(opts->flags & KG_FLAG_FULL_REORTH)) {
     int maxr = 0;
     e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantResident, t, &maxr);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -192,9 +192,10 @@ kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options*
       ctas = c;
     }
   }
-  if (variant == kg::kVariantStreaming) {
+  if (variant == kg::kVariantStreaming && (opts->flags & KG_FLAG_FULL_REORTH)) variant = kg::kVariantGenericStream;
+  if (variant == kg::kVariantStreaming || variant == kg::kVariantGenericStream) {
     int maxc = 0;
-    e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantStreaming, t, &maxc);
+    e = kg::eval_kernel_max_ctas(opts->prec, variant, t, &maxc);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (maxc < 1) return fail(KG_ERR_UNSUPPORTED, "evaluation kernel does not fit on this device");
     ctas = (opts->ctas > 0) ? opts->ctas : ntiles;
@@ -237,6 +238,7 @@ static kg_status enqueue(kg_handle* h, const double* u, const void* psi0, const 
   p.hc_amp = ch.hc_amp;
   p.dt = o.dt;
   p.bd_tol = o.breakdown_tol;
+  p.reorth = (o.flags & KG_FLAG_FULL_REORTH) ? 1 : 0;
   p.u = u;
   p.psi0 = (const double*)psi0;
   p.target = (const double*)target;
@@ -408,7 +410,7 @@ extern "C" kg_status kg_evaluate_static(const kg_chain* chain, const kg_options*
   int variant = kg::kVariantStreaming;
   int ctas = 0;
   const int tpc = kg::resident_tiles_per_cta(opts->prec);
-  if (tpc > 0) {
+  if (tpc > 0 && !(opts->flags & KG_FLAG_FULL_REORTH)) {
     int maxr = 0;
     e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantResident, t, &maxr);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -421,9 +423,10 @@ extern "C" kg_status kg_evaluate_static(const kg_chain* chain, const kg_options*
       ctas = c;
     }
   }
-  if (variant == kg::kVariantStreaming) {
+  if (variant == kg::kVariantStreaming && (opts->flags & KG_FLAG_FULL_REORTH)) variant = kg::kVariantGenericStream;
+  if (variant == kg::kVariantStreaming || variant == kg::kVariantGenericStream) {
     int maxc = 0;
-    e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantStreaming, t, &maxc);
+    e = kg::eval_kernel_max_ctas(opts->prec, variant, t, &maxc);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (maxc < 1) return fail(KG_ERR_UNSUPPORTED, "evaluation kernel does not fit on this device");
     ctas = (opts->ctas > 0) ? opts->ctas : ntiles;
@@ -633,6 +636,7 @@ kg_status kg_batch_create(kg_batch** batch, int32_t B, const kg_chain* chains, c
     p.scal = (double*)(w + pl.scal);
     p.wait_limit_ns = g_wait_limit_ns.load();
     p.debug_fault = 0;
+    p.reorth = 0;
     p.prof = nullptr;
   }
   if ((e = cudaMemcpy(ws + lay.probs, probs.data(), sizeof(kg::EvalParams) * B, cudaMemcpyHostToDevice)) ||

@@ -76,6 +76,7 @@ struct SmemSlice {
   double s_ap, s_ib, s_bk, s_alpha, s_b2, beta_m, nrm_out, s_ib0;
   float f_ap, f_ib, f_bk, f_alpha, f_ib0, f_bk0, f_beta_m;
   int code1, stop, meff, broke;
+  double rco_re[kMaxM], rco_im[kMaxM];  // re-orthogonalisation coefficients <v_i|r>
   // resident complex64 path: the Lanczos step's ring of partner-tile copies, its chunk table,
   // the float-float sums of every step (for the FP64 tridiagonal), the TMEM address
   unsigned long long lmbar[kLzStages];
@@ -335,6 +336,87 @@ __device__ __forceinline__ void apply_H_tile(const Ctx<V>& c, size_t base, const
   }
 }
 
+// Full re-orthogonalisation of step k (KG_FLAG_FULL_REORTH; App. A's remedy for the loss of
+// orthogonality): the residual r, held in r_g for the own tiles (W_{k+1} on entry), loses its
+// components on every basis vector v_0..v_k by classical Gram-Schmidt applied twice,
+//   c_i = <v_i|r>,  r <- r - sum_i c_i v_i,
+// then thread 0 records b_{k+1}^2 = ||r||^2.  v_0 is psi / ||psi|| (slot 0 holds psi itself),
+// v_i (i >= 1) are the normalised basis slots.  Coefficients are reduced two vectors at a time.
+template <class V, class A, int APT>
+__device__ __noinline__ bool reorth_cgs2(Ctx<V>& c, int k, const V* src, V* r_g) {
+  using R = typename VecTraits<V>::R;
+  SmemSlice& ss = *c.ss;
+  const int tid = threadIdx.x;
+  const int T = c.tile;
+  const R ib0 = pick_r<R>(ss.s_ib0, ss.f_ib0);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i0 = 0; i0 <= k; i0 += 2) {
+      A part[4] = {0, 0, 0, 0};
+      for (int ct = 0; ct < c.n_own; ++ct) {
+        const size_t base = c.tile_base(ct);
+#pragma unroll
+        for (int j = 0; j < APT; ++j) {
+          const int li = tid + j * kThreads;
+          if (li >= T) continue;
+          const V rv = ldv(r_g + base + li);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int i = i0 + u;
+            if (i > k) break;
+            V v = ldv(((i == 0) ? src : c.basis_slot(i)) + base + li);
+            if (i == 0) v = vmake<V>(v.x * ib0, v.y * ib0);
+            part[2 * u] += (A)(v.x * rv.x + v.y * rv.y);
+            part[2 * u + 1] += (A)(v.x * rv.y - v.y * rv.x);
+          }
+        }
+      }
+      double out[4];
+      if (!group_reduce<4>(c.g, ss.red, part, out)) return false;
+      if (tid == 0) {
+        ss.rco_re[i0] = out[0];
+        ss.rco_im[i0] = out[1];
+        if (i0 + 1 <= k) {
+          ss.rco_re[i0 + 1] = out[2];
+          ss.rco_im[i0 + 1] = out[3];
+        }
+      }
+    }
+    __syncthreads();
+    for (int ct = 0; ct < c.n_own; ++ct) {
+      const size_t base = c.tile_base(ct);
+#pragma unroll
+      for (int j = 0; j < APT; ++j) {
+        const int li = tid + j * kThreads;
+        if (li >= T) continue;
+        V rv = ldv(r_g + base + li);
+        for (int i = 0; i <= k; ++i) {
+          V v = ldv(((i == 0) ? src : c.basis_slot(i)) + base + li);
+          if (i == 0) v = vmake<V>(v.x * ib0, v.y * ib0);
+          const R a = (R)ss.rco_re[i], b = (R)ss.rco_im[i];
+          rv.x -= a * v.x - b * v.y;
+          rv.y -= a * v.y + b * v.x;
+        }
+        stv(r_g + base + li, rv);
+      }
+    }
+  }
+  A n2[1] = {0};
+  for (int ct = 0; ct < c.n_own; ++ct) {
+    const size_t base = c.tile_base(ct);
+#pragma unroll
+    for (int j = 0; j < APT; ++j) {
+      const int li = tid + j * kThreads;
+      if (li >= T) continue;
+      const V rv = ldv(r_g + base + li);
+      n2[0] += (A)(rv.x * rv.x + rv.y * rv.y);
+    }
+  }
+  double o1[1];
+  if (!group_reduce<1>(c.g, ss.red, n2, o1)) return false;
+  if (tid == 0) ss.s_b2 = o1[0];
+  return true;
+}
+
 template <class V, class A, int APT, int TPC, bool RES>
 __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double nrm_src, double uj) {
   using R = typename VecTraits<V>::R;
@@ -482,7 +564,11 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
         if (tid == 0) flag_nonfinite(p);
         return false;
       }
-      if (code == 1) {
+      const bool reorth = !RES && p.reorth && !last;
+      if (reorth) {  // the residual, orthogonalised against the whole basis, replaces W_{k+1}
+        if constexpr (!RES)
+          if (!reorth_cgs2<V, A, APT>(c, k, src, wdst)) return false;
+      } else if (code == 1) {
         // Near an invariant subspace the identity loses the small b_{k+1} to cancellation:
         // form ||W_{k+1} - alpha_k v_k||^2 explicitly (one more reduction, rare).
         A n1[1] = {0};
@@ -505,7 +591,13 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
         if (!group_reduce<1>(c.g, ss.red, n1, o1)) return false;
         if (tid == 0) ss.s_b2 = o1[0];
       }
-      if (tid == 0) lz_finish_step(ss, k, last, p.bd_tol, amax, bmax);
+      if (tid == 0) {
+        lz_finish_step(ss, k, last, p.bd_tol, amax, bmax);
+        if (reorth) {  // W_{k+1} is the orthogonalised residual: v_{k+1} = W_{k+1} / b_{k+1}
+          ss.s_ap = 0.0;
+          ss.f_ap = 0.f;
+        }
+      }
       __syncthreads();
       c.mark(3);
       if (ss.stop) break;
@@ -2024,6 +2116,7 @@ static KernelChoice choice(int t_bits) {
 // amplitudes).
 static KernelChoice pick(int prec, int variant, int t_bits) {
   if (prec == KG_PREC_C128) return choice<double2, double, 4, 1, false, kModeGeneric>(t_bits);
+  if (variant == kVariantGenericStream) return choice<float2, float, 8, 1, false, kModeGeneric>(t_bits);
   if (variant == kVariantResidentFull) return choice<float2, float, 8, 2, true, kModeResident64>(t_bits);
   if (variant == kVariantResident) return choice<float2, float, 8, 2, true, kModeGeneric>(t_bits);
   if (t_bits == 12) return choice<float2, float, 8, 1, false, kModeStream64>(t_bits);

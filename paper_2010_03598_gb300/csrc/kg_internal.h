@@ -49,6 +49,7 @@ struct EvalParams {
   int* ctrl;                // [kCtrlStatus, kCtrlAbort]
   long long wait_limit_ns;
   int debug_fault;          // 1: CTA 0 skips its arrival at the first group barrier
+  int reorth;               // full CGS2 re-orthogonalisation of every Lanczos step
   long long* prof;          // [8] phase cycles of CTA 0, or null
 };
 

@@ -9,7 +9,8 @@ namespace kg {
 
 constexpr int kThreads = 512;  // threads per CTA of the evaluation kernel
 
-enum { kVariantStreaming = 0, kVariantResident = 1, kVariantResidentFull = 2 };
+// kVariantGenericStream: the generic streaming loop whatever the tile size (full re-orthogonalisation)
+enum { kVariantStreaming = 0, kVariantResident = 1, kVariantResidentFull = 2, kVariantGenericStream = 3 };
 
 // Cooperative launch of the single-problem evaluation kernel (prec = kg_precision).
 cudaError_t launch_eval_kernel(int prec, int variant, const EvalParams& p, int ctas, cudaStream_t stream);

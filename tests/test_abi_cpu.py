@@ -82,6 +82,13 @@ def test_workspace_bytes_covers_the_vectors(lib):
     assert n1 - n0 >= 2 * 16 * 4096
 
 
+def test_full_reorthogonalisation_flag_is_accepted(lib):
+    # the flag selects another Lanczos arrangement, not more memory: the same workspace
+    st1, n1 = _ws(lib, _chain(L=12), _opts(flags=_abi.KG_FLAG_FULL_REORTH))
+    st0, n0 = _ws(lib, _chain(L=12), _opts())
+    assert st1 == st0 == _abi.KG_OK and n1 == n0
+
+
 @pytest.mark.parametrize("chain_kw,opts_kw,status", [
     (dict(L=0), {}, _abi.KG_ERR_INVALID_ARG),
     (dict(L=31), {}, _abi.KG_ERR_UNSUPPORTED),

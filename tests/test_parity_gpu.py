@@ -137,6 +137,26 @@ def test_streaming_complex64_tiles_vs_oracle(L, ctas, hc):
     check("c64", F, g, F_ref, g_ref)
 
 
+@pytest.mark.parametrize("L,m,dt,tile_bits,ctas", [(7, 32, 1.0, 0, 0), (10, 24, 0.5, 6, 5), (14, 16, 0.2, 12, 1)])
+def test_full_reorthogonalisation_vs_oracle(L, m, dt, tile_bits, ctas):
+    # KG_FLAG_FULL_REORTH: Gram-Schmidt twice against the whole basis every step, the oracle's
+    # own arrangement (Appendix A's remedy).  Long bases over large slices (m = 32 on 128
+    # amplitudes with dt = 1) are where plain three-term Lanczos loses orthogonality.
+    N = 4
+    rng = np.random.default_rng(400 + L)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    ch = oracle.Chain(L, 1.0, 0.5)
+    F_ref, g_ref, _ = oracle.evaluate(ch, u, dt, m, psi0, f, "centered")
+    A = api()
+    for prec in ("c128", "c64"):
+        F, g, rep = run_gpu(A.ChainSpec(L, 1.0, 0.5),
+                            A.Options(N, dt, m, prec=prec, tile_bits=tile_bits, ctas=ctas, reorth=True), u, psi0, f)
+        check(prec, F, g, F_ref, g_ref)
+        assert rep["breakdowns"] == 0
+
+
 @pytest.mark.parametrize("site", [0, 4, 8])
 def test_sx_control_on_other_sites(site):
     L, N, m = 9, 6, 12
