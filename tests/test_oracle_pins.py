@@ -327,3 +327,32 @@ def test_centred_gradient_uses_both_slice_ends():
     G = d["G"]
     shifted = 0.5 * (G[1:] + np.append(G[2:], G[-1]))
     assert np.abs(g_c - g_ex).max() < 0.5 * np.abs(shifted - g_ex).max()
+
+
+def test_lobatto_gradient_error_is_order_dt7():
+    # Eqs. natu_integr / natgrad integrated with the 4-point Gauss-Lobatto rule (degree 5):
+    # the per-component error falls by 2^7 when dt halves.
+    errs = _grad_errors("exact", [4, 8, 16])
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(90.0 < r < 170.0 for r in ratios), (errs, ratios)
+
+
+@pytest.mark.parametrize("L", [4, 5, 6])
+def test_lobatto_gradient_matches_the_dense_derivative(L):
+    # Against the exact propagator derivative (divided differences of the slice eigensystem,
+    # an independent route): agreement far beyond the trapezoid rule's, which pairs the same
+    # end nodes -- a wrong interior node pairing (chi at s with psi at dt - s) or wrong weights
+    # would leave an O(dt) or O(dt^3) error instead.
+    rng = np.random.default_rng(10 + L)
+    N, dt = 6, 0.2
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    ch = oracle.Chain(L, 1.0, 0.5)
+    _, g_ex = oracle.exact_gradient(ch, u, dt, psi0, f)
+    _, g_l, d = oracle.evaluate(ch, u, dt, 16, psi0, f, "exact")
+    _, g_c, _ = oracle.evaluate(ch, u, dt, 16, psi0, f, "centered")
+    err_l = np.linalg.norm(g_l - g_ex) / np.linalg.norm(g_ex)
+    err_c = np.linalg.norm(g_c - g_ex) / np.linalg.norm(g_ex)
+    assert err_l <= 1e-8 and err_l <= 1e-4 * err_c, (err_l, err_c)
+    assert d["G_interior"].shape == (N, 2)
