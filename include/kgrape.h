@@ -12,6 +12,8 @@
  *   G_j = 2 dt Im <chi_j|Hc|psi_j>, j = 0..N                                        (Eq. gradI)
  *   dF/du_{j-1} = G_j                (KG_GRAD_ZEROTH: Hc at the end of slice j, Eq. gradI)
  *   dF/du_{j-1} = (G_{j-1} + G_j)/2  (KG_GRAD_CENTERED: trapezoid over slice j, App. B last paragraph)
+ *   dF/du_{j-1} = average of G(t) over slice j by the 4-point Gauss-Lobatto rule
+ *                 (KG_GRAD_EXACT: App. B, Eqs. natu_integr and natgrad; see kg_grad_mode)
  * Gradients are of the fidelity F (the paper's are of the infidelity I = 1 - F).
  *
  * Basis convention: amplitude index i in [0, 2^L); site k (1-based) is bit k-1 of i;
@@ -58,7 +60,14 @@ typedef enum kg_precision {
 typedef enum kg_grad_mode {
   KG_GRAD_NONE = 0,        /* fidelity only (no backward sweep) */
   KG_GRAD_CENTERED = 1,    /* (G_{j-1} + G_j) / 2, the gradient fed to L-BFGS in Sec. 2 */
-  KG_GRAD_ZEROTH = 2       /* G_j (Eq. gradI) */
+  KG_GRAD_ZEROTH = 2,      /* G_j (Eq. gradI) */
+  KG_GRAD_EXACT = 3        /* the natural gradient G(t) = 2 dt Im <chi(t)|Hc|psi(t)> averaged over
+                              slice j (App. B, Eqs. natu_integr, natgrad) with the 4-point
+                              Gauss-Lobatto rule: nodes t_{j-1} + s, s = 0, (1 -+ 1/sqrt 5) dt/2, dt,
+                              weights 1/12, 5/12, 5/12, 1/12; exact up to O(dt^7) per component.
+                              The interior states come from the slices' own Krylov bases (two more
+                              recombinations per slice and direction); the workspace keeps 2N more
+                              vectors.  Not combined with checkpointing (KG_ERR_UNSUPPORTED). */
 } kg_grad_mode;
 
 typedef enum kg_hc_kind {

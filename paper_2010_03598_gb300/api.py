@@ -14,7 +14,8 @@ from . import _abi
 from ._abi import check, lib
 
 _PREC = {"c128": _abi.KG_PREC_C128, "c64": _abi.KG_PREC_C64_F64REC}
-_GRAD = {"none": _abi.KG_GRAD_NONE, "centered": _abi.KG_GRAD_CENTERED, "zeroth": _abi.KG_GRAD_ZEROTH}
+_GRAD = {"none": _abi.KG_GRAD_NONE, "centered": _abi.KG_GRAD_CENTERED, "zeroth": _abi.KG_GRAD_ZEROTH,
+         "exact": _abi.KG_GRAD_EXACT}
 
 
 @dataclasses.dataclass(frozen=True)
@@ -42,7 +43,7 @@ class Options:
     dt: float
     m: int
     prec: str = "c64"         # "c64" (complex64 state, FP64 recurrences) or "c128"
-    grad: str = "centered"    # "none", "centered", "zeroth"
+    grad: str = "centered"    # "none", "centered", "zeroth", "exact" (Gauss-Lobatto over each slice)
     ckpt_every: int = 0
     tile_bits: int = 0
     ctas: int = 0

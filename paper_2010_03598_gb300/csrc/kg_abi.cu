@@ -33,7 +33,7 @@ kg_status cuda_fail(cudaError_t e, const char* what) {
 size_t align_up(size_t x) { return (x + kg::kAlign - 1) / kg::kAlign * kg::kAlign; }
 
 struct Layout {
-  size_t ctrl = 0, bar = 0, red = 0, scal = 0, G = 0, nrm = 0, prof = 0;
+  size_t ctrl = 0, bar = 0, red = 0, scal = 0, G = 0, nrm = 0, prof = 0, Gi = 0, tint = 0;
   size_t basis = 0, traj = 0, seg = 0, chi = 0, wbuf = 0, xbuf = 0;
   size_t st_u = 0, st_psi0 = 0, st_target = 0, st_fid = 0, st_grad = 0;
   size_t total = 0;
@@ -57,9 +57,12 @@ kg_status check_args(const kg_chain* ch, const kg_options* o) {
   if (o->m < 1 || o->m > kg::kMaxM) return fail(KG_ERR_INVALID_ARG, "m must satisfy 1 <= m <= 32");
   if (o->prec != KG_PREC_C128 && o->prec != KG_PREC_C64_F64REC)
     return fail(KG_ERR_INVALID_ARG, "prec must be KG_PREC_C128 or KG_PREC_C64_F64REC");
-  if (o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED && o->grad != KG_GRAD_ZEROTH)
-    return fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, KG_GRAD_CENTERED or KG_GRAD_ZEROTH");
+  if (o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED && o->grad != KG_GRAD_ZEROTH &&
+      o->grad != KG_GRAD_EXACT)
+    return fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, _CENTERED, _ZEROTH or _EXACT");
   if (o->ckpt_every < 0) return fail(KG_ERR_INVALID_ARG, "ckpt_every must be >= 0");
+  if (o->grad == KG_GRAD_EXACT && o->ckpt_every > 0)
+    return fail(KG_ERR_UNSUPPORTED, "KG_GRAD_EXACT keeps every slice's interior states: no checkpointing");
   if (o->tile_bits != 0 && (o->tile_bits < 1 || o->tile_bits > 13))
     return fail(KG_ERR_INVALID_ARG, "tile_bits must be 0 (auto) or 1..13");
   if (o->ctas < 0 || o->ctas > kg::kMaxCtas) return fail(KG_ERR_INVALID_ARG, "ctas must be 0 (auto) or 1..2048");
@@ -96,6 +99,10 @@ Layout make_layout(const kg_chain* ch, const kg_options* o) {
   l.chi = take(o->grad == KG_GRAD_NONE ? 0 : 2 * vb);
   l.wbuf = take(2 * vb);
   l.xbuf = take(vb);
+  if (o->grad == KG_GRAD_EXACT) {  // G and psi at the two interior quadrature nodes of every slice
+    l.Gi = take(sizeof(double) * 2 * (size_t)o->N);
+    l.tint = take(vb * 2 * (size_t)o->N);
+  }
   if (o->flags & KG_FLAG_HOST_STAGING) {
     l.st_u = take(sizeof(double) * (size_t)o->N);
     l.st_psi0 = take(16 * D);
@@ -253,6 +260,8 @@ static kg_status enqueue(kg_handle* h, const double* u, const void* psi0, const 
   p.xbuf = ws + h->lay.xbuf;
   p.G = (double*)(ws + h->lay.G);
   p.nrm = (double*)(ws + h->lay.nrm);
+  p.Gi = (o.grad == KG_GRAD_EXACT) ? (double*)(ws + h->lay.Gi) : nullptr;
+  p.tint = (o.grad == KG_GRAD_EXACT) ? (void*)(ws + h->lay.tint) : nullptr;
   p.scal = (double*)(ws + h->lay.scal);
   p.bar = (unsigned long long*)(ws + h->lay.bar);
   p.red = (double*)(ws + h->lay.red);
@@ -500,6 +509,7 @@ kg_status check_batch(int B, const kg_chain* chains, const kg_options* o) {
   if (!chains || !o) return fail(KG_ERR_INVALID_ARG, "chains and options must not be NULL");
   if (o->prec != KG_PREC_C64_F64REC) return fail(KG_ERR_UNSUPPORTED, "batched evaluation runs the complex64 path only");
   if (o->flags != 0) return fail(KG_ERR_INVALID_ARG, "batched evaluation takes no flags");
+  if (o->grad == KG_GRAD_EXACT) return fail(KG_ERR_UNSUPPORTED, "batched evaluation has no KG_GRAD_EXACT");
   if (o->tile_bits != 0 || o->ctas != 0)
     return fail(KG_ERR_INVALID_ARG, "tile_bits and ctas are set by the batch schedule, not the options");
   for (int b = 0; b < B; ++b) {
@@ -637,6 +647,8 @@ kg_status kg_batch_create(kg_batch** batch, int32_t B, const kg_chain* chains, c
     p.wait_limit_ns = g_wait_limit_ns.load();
     p.debug_fault = 0;
     p.reorth = 0;
+    p.Gi = nullptr;
+    p.tint = nullptr;
     p.prof = nullptr;
   }
   if ((e = cudaMemcpy(ws + lay.probs, probs.data(), sizeof(kg::EvalParams) * B, cudaMemcpyHostToDevice)) ||

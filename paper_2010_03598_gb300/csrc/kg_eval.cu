@@ -707,7 +707,7 @@ __device__ __forceinline__ void recomb_amp(const RecombConsts& rc, size_t gi, fl
 
 template <class V, class A, int APT, bool WBASIS>
 __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm_src, double tau, V* dst, int extra,
-                                             const V* psi_other, double& nrm_dst, double2& e) {
+                                             const V* psi_other, double& nrm_dst, double2& e, bool interior = false) {
   using R = typename VecTraits<V>::R;
   const EvalParams& p = *c.p;
   SmemSlice& ss = *c.ss;
@@ -759,7 +759,7 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
         for (int i = 1; i < meff; ++i) cm *= tnorm / (float)i;
       }
       const float err = broke ? 0.f : ss.f_beta_m * cm;
-      c.err_max = fmax(c.err_max, (double)err);  // lane meff-1 of warp 0 keeps the running maximum
+      if (!interior) c.err_max = fmax(c.err_max, (double)err);  // lane meff-1 of warp 0 keeps the maximum
     }
     if constexpr (WBASIS) {
       // Slots k >= 1 hold W_k with v_k = (W_k - alpha_{k-1} v_{k-1}) / b_k, v_0 = psi/||psi||:
@@ -793,7 +793,7 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
   }
   __syncthreads();
   c.mark(4);
-  if (tid == 0 && meff > 0) c.breakdowns += ss.broke ? 1 : 0;
+  if (tid == 0 && meff > 0 && !interior) c.breakdowns += ss.broke ? 1 : 0;
   // ---- recombination dst = sum_k coef_k (basis slot k) (+ fused norms / overlaps)
   A nacc = 0, gacc = 0;
   double ex0 = 0.0, ex1 = 0.0;
@@ -1784,6 +1784,17 @@ __device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_sr
   return finish_slice<V, A, APT, MODE == kModeResident64>(c, src, nrm_src, tau, dst, extra, psi_other, nrm_dst, e);
 }
 
+// Another step of length tau from the Krylov basis the last krylov_slice built (the basis
+// slots and T are still in place): psi(tau) at an interior quadrature node of the slice
+// (KG_GRAD_EXACT), with the same fused overlaps.
+template <class V, class A, int APT, int TPC, bool RES, int MODE>
+__device__ __noinline__ bool interior_step(Ctx<V>& c, const V* src, double nrm_src, double tau, V* dst, int extra,
+                                           const V* psi_other, double2& e) {
+  double nrm_dst;
+  return finish_slice<V, A, APT, MODE == kModeResident64>(c, src, nrm_src, tau, dst, extra, psi_other, nrm_dst, e,
+                                                          true);
+}
+
 // chi_N = beta f, ||chi_N||, and G_N = 2 dt Im <chi_N|Hc|psi_N>.
 template <class V>
 __device__ bool init_costate(Ctx<V>& c, double2 beta, V* chi, const V* psiN, double& nrm, double& gim) {
@@ -1858,6 +1869,12 @@ __device__ __forceinline__ V* fwd_slot(const Ctx<V>& c, int j) {
   return (V*)p.seg + (size_t)(C - 1 + (j & 1)) * c.D;
 }
 
+// Interior node a (0, 1) of the 4-point Gauss-Lobatto rule on [0, dt]: (1 -+ 1/sqrt 5) dt / 2.
+__device__ __forceinline__ double lobatto_node(double dt, int a) {
+  const double s1 = 0.5 * dt * (1.0 - 0.4472135954999579);  // 1/sqrt(5)
+  return (a == 0) ? s1 : dt - s1;
+}
+
 // One whole evaluation (forward sweep, overlap, co-state sweep, gradient) of problem p by the
 // group of `size` CTAs in which this CTA has rank `rank`.  Returns false if the group aborted.
 template <class V, class A, int APT, int TPC, bool RES, int MODE>
@@ -1920,6 +1937,15 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
     if (!krylov_slice<V, A, APT, TPC, RES, MODE>(c, fwd_slot<V>(c, j - 1), nrm_prev, p.u[j - 1], p.dt, fwd_slot<V>(c, j),
                                            extra, nullptr, nrm_new, e))
       return false;
+    if (p.grad_mode == KG_GRAD_EXACT) {  // psi at the slice's interior quadrature nodes (ckpt == 0)
+      for (int a = 0; a < 2; ++a) {
+        double2 ei;
+        V* d = (V*)p.tint + (size_t)(2 * (j - 1) + a) * c.D;
+        if (!interior_step<V, A, APT, TPC, RES, MODE>(c, fwd_slot<V>(c, j - 1), nrm_prev, lobatto_node(p.dt, a), d,
+                                                      kExtraNone, nullptr, ei))
+          return false;
+      }
+    }
     if (lead) p.nrm[j] = nrm_new;
     nrm_prev = nrm_new;
     if (j == p.N) beta = e;
@@ -1970,6 +1996,17 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
                                                kExtraGradOverlap, psi_jm1, nn, e))
           return false;
         if (lead) p.G[j - 1] = 2.0 * p.dt * e.x;
+        if (p.grad_mode == KG_GRAD_EXACT) {
+          // chi at t_{j-1} + s = exp(+i (dt - s) H_j) chi_j, overlapped with the stored psi there
+          for (int a = 0; a < 2; ++a) {
+            double2 ei;
+            const V* psi_s = (const V*)p.tint + (size_t)(2 * (j - 1) + a) * c.D;
+            if (!interior_step<V, A, APT, TPC, RES, MODE>(c, chi[cur], nchi, -(p.dt - lobatto_node(p.dt, a)),
+                                                          (V*)p.wbuf, kExtraGradOverlap, psi_s, ei))
+              return false;
+            if (lead) p.Gi[2 * (j - 1) + a] = 2.0 * p.dt * ei.x;
+          }
+        }
         cur ^= 1;
         nchi = nn;
       }
@@ -1981,7 +2018,10 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
     if (p.grad_mode != KG_GRAD_NONE) {
       for (int j = threadIdx.x; j < p.N; j += blockDim.x) {
         const double gl = p.G[j], gr = p.G[j + 1];
-        p.grad[j] = (p.grad_mode == KG_GRAD_ZEROTH) ? gr : 0.5 * (gl + gr);
+        if (p.grad_mode == KG_GRAD_EXACT)  // Gauss-Lobatto weights 1/12, 5/12, 5/12, 1/12
+          p.grad[j] = (gl + gr) / 12.0 + 5.0 * (p.Gi[2 * j] + p.Gi[2 * j + 1]) / 12.0;
+        else
+          p.grad[j] = (p.grad_mode == KG_GRAD_ZEROTH) ? gr : 0.5 * (gl + gr);
       }
     }
     double em = (threadIdx.x < 32) ? warp_max(c.err_max) : 0.0;

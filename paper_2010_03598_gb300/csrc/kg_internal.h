@@ -42,6 +42,8 @@ struct EvalParams {
   void* xbuf;               // 1 vector: tile-leaving part of H v_k (streaming variant)
   double* G;                // [N+1] overlaps
   double* nrm;              // [N+1] ||psi_j|| of the forward sweep
+  double* Gi;               // [2N] G at the interior Gauss-Lobatto nodes (KG_GRAD_EXACT), or null
+  void* tint;               // [2N] psi at the interior nodes of every slice (KG_GRAD_EXACT), or null
   double* scal;             // [kScCount]
   unsigned long long* bar;  // group barrier counter
   double* red;              // [2][red_stride][kNRed] reduction slots

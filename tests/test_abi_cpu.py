@@ -82,6 +82,17 @@ def test_workspace_bytes_covers_the_vectors(lib):
     assert n1 - n0 >= 2 * 16 * 4096
 
 
+def test_exact_gradient_workspace_and_limits(lib):
+    # KG_GRAD_EXACT keeps psi at two interior nodes of every slice (2N more vectors, 2N doubles)
+    N, L = 40, 12
+    st0, n0 = _ws(lib, _chain(L=L), _opts(N=N, grad=_abi.KG_GRAD_CENTERED))
+    st1, n1 = _ws(lib, _chain(L=L), _opts(N=N, grad=_abi.KG_GRAD_EXACT))
+    assert st0 == st1 == _abi.KG_OK
+    assert n1 - n0 >= 2 * N * (1 << L) * 8
+    st, _ = _ws(lib, _chain(L=L), _opts(N=N, grad=_abi.KG_GRAD_EXACT, ckpt_every=5))
+    assert st == _abi.KG_ERR_UNSUPPORTED
+
+
 def test_full_reorthogonalisation_flag_is_accepted(lib):
     # the flag selects another Lanczos arrangement, not more memory: the same workspace
     st1, n1 = _ws(lib, _chain(L=12), _opts(flags=_abi.KG_FLAG_FULL_REORTH))

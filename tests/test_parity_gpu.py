@@ -157,6 +157,40 @@ def test_full_reorthogonalisation_vs_oracle(L, m, dt, tile_bits, ctas):
         assert rep["breakdowns"] == 0
 
 
+@pytest.mark.parametrize("L,N,m,dt,tile_bits,ctas", [(8, 24, 12, 0.1, 0, 0), (10, 6, 12, 0.3, 6, 3),
+                                                      (14, 5, 16, 0.05, 12, 1), (16, 6, 20, 0.05, 0, 0)])
+def test_exact_gradient_vs_oracle(L, N, m, dt, tile_bits, ctas):
+    # KG_GRAD_EXACT (App. B, Eqs. natu_integr / natgrad by Gauss-Lobatto quadrature): generic
+    # (L=8, L=10 on ragged tiles), complex64 streaming (L=14 on one CTA) and resident (L=16).
+    rng = np.random.default_rng(500 + L)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    ch = oracle.Chain(L, 1.0, 0.5)
+    F_ref, g_ref, _ = oracle.evaluate(ch, u, dt, m, psi0, f, "exact")
+    A = api()
+    for prec in ("c128", "c64"):
+        F, g, rep = run_gpu(A.ChainSpec(L, 1.0, 0.5),
+                            A.Options(N, dt, m, prec=prec, grad="exact", tile_bits=tile_bits, ctas=ctas), u, psi0, f)
+        check(prec, F, g, F_ref, g_ref)
+        assert rep["breakdowns"] == 0
+
+
+def test_exact_gradient_matches_the_dense_derivative():
+    # Against the exact propagator derivative of the dense oracle (an independent route):
+    # the quadrature leaves O(dt^7) per component, far below the trapezoid rule's O(dt^3).
+    L, N, dt, m = 6, 8, 0.2, 16
+    rng = np.random.default_rng(61)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    _, g_ex = oracle.exact_gradient(oracle.Chain(L, 1.0, 0.5), u, dt, psi0, f)
+    A = api()
+    _, g, _ = run_gpu(A.ChainSpec(L, 1.0, 0.5), A.Options(N, dt, m, prec="c128", grad="exact"), u, psi0, f)
+    _, gc, _ = run_gpu(A.ChainSpec(L, 1.0, 0.5), A.Options(N, dt, m, prec="c128", grad="centered"), u, psi0, f)
+    assert nrel(g, g_ex) <= 1e-8 and nrel(g, g_ex) <= 1e-4 * nrel(gc, g_ex)
+
+
 @pytest.mark.parametrize("site", [0, 4, 8])
 def test_sx_control_on_other_sites(site):
     L, N, m = 9, 6, 12
