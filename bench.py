@@ -46,6 +46,9 @@ def parse_args():
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--N", type=int, default=0, help="shorter pulse (profiling a small case); 0 = workload's N")
+    ap.add_argument("--grad", choices=["centered", "zeroth", "exact"], default="centered",
+                    help="gradient mode of the timed evaluations (the headline is the centred gradient)")
+    ap.add_argument("--reorth", action="store_true", help="full re-orthogonalisation of every Lanczos step")
     return ap.parse_args()
 
 
@@ -60,19 +63,22 @@ def workload(name, N: int = 0):
     return W, w
 
 
-def alg_bytes(w, prec: str, ckpt: int = 0) -> int:
+def alg_bytes(w, prec: str, ckpt: int = 0, grad: str = "centered") -> int:
     """Algorithmic HBM bytes of one evaluation: D-vector passes of the basis-storing Lanczos.
 
     Per slice and direction: Lanczos step k reads v_k and v_{k-1} (k >= 1) and writes
     v_{k+1} (k <= m-2): 3m-2 passes; the recombination reads m vectors and writes 1: m+1.
     The backward sweep reads psi_j once more for the gradient overlap; the target overlap
     reads 2 vectors.  P = N (2 (4m-1) + 1) + 2, plus N (4m-1) when checkpoints are
-    recomputed.
+    recomputed, plus N (4 (m+1) + 2) for the exact gradient (two more recombinations per
+    slice and direction, and the stored interior states read once).
     """
     s = 16 if prec == "c128" else 8
     P = w.N * (2 * (4 * w.m - 1) + 1) + 2
     if ckpt:
         P += w.N * (4 * w.m - 1)
+    if grad == "exact":  # two more recombinations per slice each way, and the stored interior states
+        P += w.N * (4 * (w.m + 1) + 2)
     return P * w.D * s
 
 
@@ -269,7 +275,7 @@ def run_ours(args):
 
     def timed(prec, steps, warmup):
         eng = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec=prec, tile_bits=args.tile_bits, ctas=args.ctas,
-                                        ckpt_every=w.ckpt), device=dev)
+                                        ckpt_every=w.ckpt, grad=args.grad, reorth=args.reorth), device=dev)
         for _ in range(warmup):
             eng.evaluate(ut, pt, ft)
         rep = eng.sync()
@@ -309,7 +315,7 @@ def run_ours(args):
     ms_per_step = total_s * 1e3 / args.steps
     hbm, peak_kind = measured_peaks()
     per_launch_s = statistics.mean(ms) / 1e3
-    ab = alg_bytes(w, args.prec, w.ckpt)
+    ab = alg_bytes(w, args.prec, w.ckpt, args.grad)
     achieved = ab / per_launch_s / 1e9
     kernel_key = f"kg_eval_kernel<{'float2' if args.prec == 'c64' else 'double2'}>@{args.workload}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -336,6 +342,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, w)
+        if args.grad != "centered" and cpu.get("sample"):
+            cpu["sample"] += "; the oracle's centred gradient, not the timed gradient mode"
     emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, fp64, rep, fid, wall)
     if world > 1:
         dist.destroy_process_group()
@@ -344,7 +352,8 @@ def run_ours(args):
 def run_e2e(A, chain, w, args, dev, u, psi0, f, barrier, max_over_ranks, world):
     import torch
     eng = A.KGrape(chain, A.Options(w.N, w.dt, w.m, prec=args.prec, host_staging=True, tile_bits=args.tile_bits,
-                                    ctas=args.ctas, ckpt_every=w.ckpt), device=dev)
+                                    ctas=args.ctas, ckpt_every=w.ckpt, grad=args.grad, reorth=args.reorth),
+                   device=dev)
     uh = torch.tensor(u).pin_memory()
     ph = torch.tensor(psi0).pin_memory()
     fh = torch.tensor(f).pin_memory()
@@ -369,7 +378,8 @@ def emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, f
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+f64" if args.prec == "c64" else "c128", "data": "synthetic",
-            "config": config_block(w, args.workload, args.prec), "roofline": roofline, "cpu_baseline": cpu,
+            "config": dict(config_block(w, args.workload, args.prec), grad=args.grad, reorth=bool(args.reorth)),
+            "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps, "fp64_path": fp64,
             "report": {k: rep[k] for k in ("krylov_err_max", "norm_final", "breakdowns", "ctas", "tile_bits",
                                            "threads")},
