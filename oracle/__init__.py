@@ -15,6 +15,8 @@ Modules (each function cites the passage of the paper it follows):
                and the zeroth-order / centred gradients (Sec. 2, App. B)
 * ``dense``  - dense eigendecomposition propagators and the exact gradient for
                small chains (App. B)
+* ``sector`` - the chain in a parity-excitation subspace (Sec. 3.1): sector states,
+               parity eigenbasis Q, H_red = Q H Q^T, with the ``Chain`` interface
 
 Every function is pinned by tests marked "not gpu" against results that do not
 come from the oracle itself (Kronecker-product Hamiltonians, closed forms at L=1
@@ -24,8 +26,10 @@ from .chain import Chain
 from .krylov import expm_e1, krylov_step, lanczos, tridiag
 from .grape import evaluate, forward, overlaps_G, segment_forward_backward
 from .dense import exact_fidelity, exact_forward, exact_gradient
+from .sector import SectorChain, paper_chain
 
 __all__ = [
     "Chain", "expm_e1", "krylov_step", "lanczos", "tridiag", "evaluate", "forward",
     "overlaps_G", "segment_forward_backward", "exact_fidelity", "exact_forward", "exact_gradient",
+    "SectorChain", "paper_chain",
 ]

@@ -131,3 +131,47 @@ def fd_indices(w: Workload, count: int = 16) -> list[int]:
     """Seeded slice indices for central finite-difference checks of the gradient."""
     rng = np.random.default_rng([w.seed, 999])
     return sorted(int(i) for i in rng.choice(w.N, count, replace=False))
+
+
+# ---------------------------------------------------------------- the paper's own workload
+@dataclasses.dataclass(frozen=True)
+class SectorWorkload:
+    """Sec. 3.1-3.2: K excitations of an L-site XXZ chain, even parity, e_1 -> e_D.
+
+    J = 1, alpha_z = 0.5 (Eq. H01), Hc = (J/2)(sigma^z_1 + sigma^z_L), dt = 0.5, m = 10 Krylov
+    vectors, M = 4D controls drawn from U(-1, 1).  D (the subspace dimension) is not stored
+    here: it comes from whoever builds the basis, and sets N = n_per_dim * D.
+    """
+
+    name: str
+    L: int
+    K: int
+    parity: int = 1
+    J: float = 1.0
+    alpha_z: float = 0.5
+    dt: float = 0.5
+    m: int = 10
+    n_per_dim: int = 4
+    seed: int = SEED_BASE + 6
+
+
+SECTOR_WORKLOADS = {
+    "pe_L10_K4": SectorWorkload("pe_L10_K4", L=10, K=4),
+    "pe_L14_K4": SectorWorkload("pe_L14_K4", L=14, K=4),
+    "pe_L20_K4": SectorWorkload("pe_L20_K4", L=20, K=4),
+}
+
+
+def sector_instance(w: SectorWorkload, D: int, batch: int = 1, N: int | None = None):
+    """Controls of `batch` independent pulses and the task e_1 -> e_D of a D-dimensional subspace.
+
+    Pulse b draws its N (default n_per_dim * D) controls from default_rng([seed, b]).  Returns
+    (u[batch, N] float64, psi0[D] complex128 = e_1, target[D] complex128 = e_D).
+    """
+    n = w.n_per_dim * D if N is None else N
+    u = np.stack([draw_controls(np.random.default_rng([w.seed, b]), n) for b in range(batch)])
+    psi0 = np.zeros(D, dtype=np.complex128)
+    psi0[0] = 1.0
+    target = np.zeros(D, dtype=np.complex128)
+    target[D - 1] = 1.0
+    return u, psi0, target
