@@ -250,6 +250,84 @@ kg_status kg_batch_destroy(kg_batch* batch);
 kg_status kg_evaluate_static(const kg_chain* chain, const kg_options* opts, const double* u, const void* psi0,
                              const void* target, double* fid, double* grad, void* cuda_stream);
 
+/* ---------------------------------------------------------------- parity-excitation subspaces
+ * Sec. 3.1's own setting.  H0 and a diagonal control Hc = hc_amp * sum_{s in mask} Sz_s keep the
+ * number of excitations fixed (set bits of the basis index, i.e. spins down) and, when the mask is
+ * mirror-symmetric, commute with the parity Pi that mirrors the chain (bit b <-> bit L-1-b).  An
+ * evaluation can then run in one parity-excitation (PE) subspace, which Sec. 3.1 builds by
+ * diagonalising Pi on the K-excitation sector and reducing H0 and Hc to the eigenvectors of the
+ * wanted parity.  Basis of the subspace (K excitations, parity p):
+ *   p = +1: (|s> + |Pi s>)/sqrt 2 for every orbit {s, Pi s} with s < Pi s, and |s> for s = Pi s;
+ *   p = -1: (|s> - |Pi s>)/sqrt 2 for every orbit with s < Pi s (palindromes have even parity);
+ *   p =  0: |s> for every s with K set bits (no parity reduction);
+ * ordered by s ascending (Sec. 3.1 orders the reduced basis by the binary number of the bit string;
+ * the smaller member of an orbit is the same whichever end the number starts from).  For states in
+ * the subspace, F and the gradient equal those of the full 2^L chain.  Vectors (psi0, target) are
+ * complex128 in this basis; the Krylov sweeps, gradient modes and precisions are those of
+ * kg_evaluate.  Each problem of a batch (one control pulse each) runs on one CTA, with the whole
+ * state in shared memory; CTAs take problems b, b + grid, b + 2 grid, ...  No device-side wait. */
+typedef struct kg_sector {
+  int32_t L;               /* number of spins, 2 <= L <= 30 */
+  int32_t K;               /* excitations (set bits), 0 <= K <= L */
+  int32_t parity;          /* +1 even, -1 odd, 0 the whole K-excitation sector */
+  int32_t reserved0;       /* must be 0 */
+  uint64_t hc_site_mask;   /* sites of the Sz terms of Hc (bits < L); mirror-symmetric if parity != 0 */
+  double Jxy;              /* as kg_chain: flip-flop coupling per bond */
+  double Jz;               /* as kg_chain: Ising coupling per bond */
+  double hc_amp;           /* amplitude of Hc.  Sec. 3.1's drift (J/2) sum sigma.sigma with alpha_z, and
+                              control (J/2)(sigma^z_1 + sigma^z_L), are Jxy = 2J, Jz = 2J alpha_z,
+                              hc_amp = J, mask = sites 1 and L */
+} kg_sector;
+
+typedef struct kg_sector_handle kg_sector_handle;  /* opaque host object; owns no device memory */
+
+/* Dimension D of the subspace (host only).  KG_ERR_INVALID_ARG for bad fields; KG_ERR_UNSUPPORTED
+ * when D exceeds what one CTA holds (the limit depends on prec; see kg_sector_workspace_bytes). */
+kg_status kg_sector_dim(const kg_sector* sector, int32_t* D);
+
+/* The smaller member s of every basis vector's orbit, in basis order (host array of D entries;
+ * host only).  Use it to place states of the full chain in the subspace and back. */
+kg_status kg_sector_states(const kg_sector* sector, uint64_t* states, int32_t D);
+
+/* H0 v on the host, from the same basis and tables the kernel uses (a check of the reduction
+ * that needs no GPU): v, w host arrays of D complex128.  Hc is diagonal: hc_amp/2 (popcount(mask)
+ * - 2 popcount(s_r & mask)) on row r. */
+kg_status kg_sector_apply_h0(const kg_sector* sector, const double* v, double* w, int32_t D);
+
+/* Workspace bytes for B pulses with options opts (N, m <= 32, prec, grad NONE / CENTERED / ZEROTH,
+ * dt, breakdown_tol, ctas = most CTAs to use (0 = every one that fits); ckpt_every and tile_bits
+ * must be 0; flags: KG_FLAG_PHASE_TIMING only, recording CTA 0's cycles in kg_report.phase_cycles as
+ * [0] Lanczos gathers and updates, [1] block reductions, [4] tridiagonal T and small exponential,
+ * [5] recombination, [6] pulse setup and overlaps, [7] total).  The workspace holds one trajectory psi_0..psi_N per CTA of the launch, so it
+ * is sized for the grid kg_sector_create will choose on the current device (min(B, resident CTAs,
+ * ctas); B CTAs if no device is visible).  KG_ERR_UNSUPPORTED for KG_GRAD_EXACT, checkpoints, or a
+ * subspace too large for one CTA's shared memory. */
+kg_status kg_sector_workspace_bytes(const kg_sector* sector, const kg_options* opts, int32_t B, size_t* bytes);
+
+/* Create a handle for B pulses on the current device, a caller-owned 256-byte aligned workspace of
+ * at least kg_sector_workspace_bytes and a CUDA stream (NULL = legacy default stream).  Builds the
+ * subspace's tables on the host and copies them into the workspace (synchronously). */
+kg_status kg_sector_create(kg_sector_handle** handle, const kg_sector* sector, const kg_options* opts,
+                           int32_t B, void* workspace, size_t bytes, void* cuda_stream);
+
+/* Evaluate B pulses, asynchronous on the handle's stream (one kernel launch).  Device pointers:
+ *   u      [B][N] float64: pulse b's controls, u[b][j-1] acts in slice j
+ *   psi0   [D] complex128: initial state (shared by all pulses)
+ *   target [D] complex128: target state f (shared; normalised by the caller)
+ *   fid    [B] float64: F_b = |<f|psi_N>|^2
+ *   grad   [B][N] float64: dF_b/du_b (NULL only with KG_GRAD_NONE)
+ * psi0/target 16-byte aligned, the others 8-byte aligned. */
+kg_status kg_sector_evaluate(kg_sector_handle* handle, const double* u, const void* psi0, const void* target,
+                             double* fid, double* grad);
+
+/* Wait for the stream; return the device status (KG_ERR_NONFINITE if a Lanczos coefficient or a
+ * norm was not finite; KG_ERR_TIMEOUT if a pulse ran longer than 60 times the kg_set_wait_limit_ns
+ * limit, i.e. 2 minutes by default, checked at every slice).  rep (nullable): beta and norm_final of pulse 0, the largest Krylov error
+ * indicator and the total breakdowns over all pulses, the grid (ctas) and threads per CTA. */
+kg_status kg_sector_sync(kg_sector_handle* handle, kg_report* rep);
+
+kg_status kg_sector_destroy(kg_sector_handle* handle);
+
 /* Test hook for failure detection.  kind 1: in the next launch, CTA 0 does not arrive at
  * the first group barrier (a member that never joins); the other CTAs' waits, and its own,
  * run out after the wait limit and the launch ends with KG_ERR_TIMEOUT (read by kg_sync).

@@ -43,6 +43,12 @@ class KgBatchSchedule(ctypes.Structure):
                 ("reserved1", ctypes.c_int32)]
 
 
+class KgSector(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("K", ctypes.c_int32), ("parity", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("hc_site_mask", ctypes.c_uint64), ("Jxy", ctypes.c_double),
+                ("Jz", ctypes.c_double), ("hc_amp", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
 
@@ -70,6 +76,16 @@ SIGNATURES = {
     "kg_batch_destroy": (ctypes.c_int, [_P]),
     "kg_evaluate_static": (ctypes.c_int, [ctypes.POINTER(KgChain), ctypes.POINTER(KgOptions), _P, _P, _P, _P, _P,
                                           _P]),
+    "kg_sector_dim": (ctypes.c_int, [ctypes.POINTER(KgSector), ctypes.POINTER(ctypes.c_int32)]),
+    "kg_sector_states": (ctypes.c_int, [ctypes.POINTER(KgSector), ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
+    "kg_sector_apply_h0": (ctypes.c_int, [ctypes.POINTER(KgSector), _P, _P, ctypes.c_int32]),
+    "kg_sector_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(KgSector), ctypes.POINTER(KgOptions), ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "kg_sector_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(KgSector), ctypes.POINTER(KgOptions),
+                                        ctypes.c_int32, _P, ctypes.c_size_t, _P]),
+    "kg_sector_evaluate": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "kg_sector_sync": (ctypes.c_int, [_P, ctypes.POINTER(KgReport)]),
+    "kg_sector_destroy": (ctypes.c_int, [_P]),
 }
 
 _lib = None

@@ -261,3 +261,117 @@ class KGrapeBatch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- parity-excitation subspaces
+@dataclasses.dataclass(frozen=True)
+class SectorSpec:
+    """K excitations of an L-site XXZ chain in one parity subspace (Sec. 3.1); Hc = hc_amp sum Sz over mask."""
+
+    L: int
+    K: int
+    parity: int = 1           # +1 even, -1 odd, 0 the whole K-excitation sector
+    Jxy: float = 2.0          # Sec. 3.1 with J = 1, alpha_z = 0.5: Jxy = 2 J, Jz = 2 J alpha_z
+    Jz: float = 1.0
+    hc_mask: int | None = None  # default: sites 1 and L
+    hc_amp: float = 1.0       # Sec. 3.1: (J/2)(sigma^z_1 + sigma^z_L) = J (Sz_1 + Sz_L)
+
+    def to_c(self) -> _abi.KgSector:
+        mask = (1 | (1 << (self.L - 1))) if self.hc_mask is None else int(self.hc_mask)
+        return _abi.KgSector(self.L, self.K, self.parity, 0, mask, self.Jxy, self.Jz, self.hc_amp)
+
+
+def sector_dim(spec: SectorSpec) -> int:
+    D = ctypes.c_int32(0)
+    check(lib().kg_sector_dim(ctypes.byref(spec.to_c()), ctypes.byref(D)), "kg_sector_dim")
+    return int(D.value)
+
+
+def sector_states(spec: SectorSpec):
+    """The smaller member s_r of every basis vector's orbit, in basis order (numpy uint64)."""
+    import numpy as np
+
+    D = sector_dim(spec)
+    out = np.zeros(D, dtype=np.uint64)
+    check(lib().kg_sector_states(ctypes.byref(spec.to_c()), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), D),
+          "kg_sector_states")
+    return out
+
+
+def sector_apply_h0(spec: SectorSpec, v):
+    """H0 v on the host with the kernel's own tables (numpy complex128 in, out): a check, no GPU."""
+    import numpy as np
+
+    v = np.ascontiguousarray(v, dtype=np.complex128)
+    w = np.zeros_like(v)
+    check(lib().kg_sector_apply_h0(ctypes.byref(spec.to_c()), v.ctypes.data, w.ctypes.data, v.shape[0]),
+          "kg_sector_apply_h0")
+    return w
+
+
+def sector_workspace_bytes(spec: SectorSpec, opts: Options, B: int) -> int:
+    n = ctypes.c_size_t(0)
+    check(lib().kg_sector_workspace_bytes(ctypes.byref(spec.to_c()), ctypes.byref(opts.to_c()), B, ctypes.byref(n)),
+          "kg_sector_workspace_bytes")
+    return int(n.value)
+
+
+class KGrapeSector:
+    """B pulses of one parity-excitation subspace problem, one CTA per pulse (one launch per call).
+
+    ``evaluate(u[B, N], psi0[D], target[D])`` enqueues F and dF/du of every pulse and returns the
+    device tensors (fid[B], grad[B, N]); ``sync()`` waits and returns the report.
+    """
+
+    def __init__(self, spec: SectorSpec, opts: Options, B: int = 1, device=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("KGrapeSector needs a CUDA device; there is no CPU fallback")
+        self.spec, self.opts, self.B = spec, opts, int(B)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.D = sector_dim(spec)
+        nbytes = sector_workspace_bytes(spec, opts, self.B)
+        self._ws_raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws_raw.data_ptr() + ((-self._ws_raw.data_ptr()) % 256)
+        self.workspace_bytes = nbytes
+        h = ctypes.c_void_p(0)
+        with torch.cuda.device(self.device):
+            check(lib().kg_sector_create(ctypes.byref(h), ctypes.byref(spec.to_c()), ctypes.byref(opts.to_c()),
+                                         self.B, ctypes.c_void_p(base), ctypes.c_size_t(nbytes),
+                                         ctypes.c_void_p(self.stream.cuda_stream)), "kg_sector_create")
+        self._h = h
+        self.fid = torch.zeros(self.B, dtype=torch.float64, device=self.device)
+        self.grad = torch.zeros(self.B, max(opts.N, 1), dtype=torch.float64, device=self.device)
+
+    def evaluate(self, u: torch.Tensor, psi0: torch.Tensor, target: torch.Tensor):
+        B, N, D = self.B, self.opts.N, self.D
+        if u.dtype != torch.float64 or tuple(u.shape) != (B, N) or not u.is_contiguous() or u.device != self.device:
+            raise ValueError(f"u must be a contiguous float64 tensor of shape ({B}, {N}) on {self.device}")
+        for name, t in (("psi0", psi0), ("target", target)):
+            if t.dtype != torch.complex128 or t.numel() != D or not t.is_contiguous() or t.device != self.device:
+                raise ValueError(f"{name} must be a contiguous complex128 tensor of {D} amplitudes on {self.device}")
+        with torch.cuda.device(self.device):
+            check(lib().kg_sector_evaluate(self._h, _ptr(u), _ptr(psi0), _ptr(target), _ptr(self.fid),
+                                           _ptr(self.grad) if self.opts.grad != "none" else None),
+                  "kg_sector_evaluate")
+        return self.fid, self.grad[:, :N]
+
+    def sync(self) -> dict:
+        rep = _abi.KgReport()
+        with torch.cuda.device(self.device):
+            check(lib().kg_sector_sync(self._h, ctypes.byref(rep)), "kg_sector_sync")
+        out = {f: getattr(rep, f) for f, _ in rep._fields_}
+        out["phase_cycles"] = list(rep.phase_cycles)
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().kg_sector_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -22,7 +22,7 @@ LIB = os.path.join(PKG, "libkgrape.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
            "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["kg_eval.cu", "kg_abi.cu"]
+SOURCES = ["kg_eval.cu", "kg_abi.cu", "kg_sector.cu"]
 
 
 def nvcc() -> str:

@@ -124,6 +124,13 @@ int default_tile_bits(const kg_chain* ch, const kg_options* o) {
 
 }  // namespace
 
+namespace kg {
+// Failures of the other host translation units go through the same thread-local message.
+kg_status host_fail(kg_status st, const std::string& msg) { return fail(st, msg); }
+// Time limit of one pulse of a subspace launch: 60 device-side wait limits (2 minutes by default).
+long long sector_time_limit_ns() { return 60LL * g_wait_limit_ns.load(); }
+}  // namespace kg
+
 struct kg_handle {
   kg_chain chain;
   kg_options opts;

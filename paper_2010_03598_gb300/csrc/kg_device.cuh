@@ -483,11 +483,14 @@ __device__ __constant__ double kInvFact[41] = {
 // c = exp(-i tau T) e_1 for the real symmetric tridiagonal T of order n <= 32
 // (diag alpha[0..n-1], off-diagonal beta[1..n-1]; beta[k] couples k-1 and k),
 // executed by one full warp; lane k holds c_k.  Method: split tau into s equal steps with
-// ||(tau/s) T||_inf <= 1 (Gershgorin row sums) and, with A = (tau/s) T, sum the Taylor
+// ||(tau/s) T||_inf <= 4 (Gershgorin row sums) and, with A = (tau/s) T, sum the Taylor
 // series exp(-i A) y = sum_p (-i)^p A^p y / p!  until the remainder bound r^(K+1)/(K+1)!
-// drops below `tol`.  A is real, so for real y every A^p y is real and (-i)^p only picks
-// the real or the imaginary part and a sign; a complex y is two real series.  ||A|| <= 1
-// keeps A^p y bounded.  FP64 throughout (about four FP64 operations per term and part).
+// drops below `tol` (r <= 4: at most 33 terms for tol = 1e-18).  A is real, so for real y
+// every A^p y is real and (-i)^p only picks the real or the imaginary part and a sign; a
+// complex y is two real series.  The first step starts from the real e_1, so a single step
+// (||tau T|| <= 4, the common case) is one real series.  With ||A|| <= 4 the largest term is
+// 4^4/4! < 11 times ||y||, so rounding stays below ~1e-14 ||y||.  FP64 throughout (about four
+// FP64 operations per term and part).
 __device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const double* beta, const float* alpha_f,
                                                 const float* beta_f, int n, double tau, float tau_f, double tol,
                                                 double& c_re, double& c_im, float& tnorm) {
@@ -503,11 +506,11 @@ __device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const doubl
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) row = fmaxf(row, __shfl_xor_sync(0xffffffffu, row, o));
   tnorm = row;
-  int s = (int)ceilf(row * 1.0001f);
+  int s = (int)ceilf(row * 1.0001f * 0.25f);
   if (s < 1) s = 1;
   const double h = (s == 1) ? tau : tau / (double)s;
   const double ha = h * a, hbl = h * bl, hbh = h * bh;  // rows of A = h T
-  const float r = row * 1.0001f / (float)s;             // <= 1 bound of ||A||
+  const float r = row * 1.0001f / (float)s;             // <= 4 bound of ||A||
   int K = 0;
   {
     float rem = r;  // r^(K+1) / (K+1)!, the first omitted term's bound

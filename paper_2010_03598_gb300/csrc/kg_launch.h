@@ -3,7 +3,10 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "kg_internal.h"
+#include "kgrape.h"
 
 namespace kg {
 
@@ -25,5 +28,11 @@ int resident_tiles_per_cta(int prec);
 // Batched evaluation kernel (complex64): cooperative launch (CUDA-graph capturable).
 cudaError_t launch_batch_kernel(const BatchParams& bp, int ctas, cudaStream_t stream);
 cudaError_t batch_kernel_max_ctas(int* out);
+
+// Record msg as the calling thread's last error (kg_last_error) and return st.
+kg_status host_fail(kg_status st, const std::string& msg);
+
+// Time limit of one pulse of a subspace launch (ns), derived from kg_set_wait_limit_ns.
+long long sector_time_limit_ns();
 
 }  // namespace kg

@@ -1,0 +1,92 @@
+"""Host side of the parity-excitation subspace entry points (no GPU): the basis and the kernel's
+H0 tables against the oracle's Sec. 3.1 reduction (index work bit-exact), and argument checks."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle.sector as S
+from paper_2010_03598_gb300 import _abi
+from paper_2010_03598_gb300 import api as A
+
+CASES = [(10, 4, 1), (14, 4, 1), (20, 4, 1), (8, 3, -1), (9, 4, 0), (5, 2, 1), (3, 1, 1), (12, 6, 1), (12, 6, -1),
+         (2, 1, 1), (2, 1, -1), (6, 0, 1), (7, 7, 1), (17, 4, 1)]
+
+
+@pytest.mark.parametrize("L,K,parity", CASES)
+def test_basis_states_equal_the_oracles(L, K, parity):
+    spec = A.SectorSpec(L, K, parity)
+    st = A.sector_states(spec).astype(np.int64)
+    reps = S.pe_change_of_basis(S.k_sector_states(L, K), L, parity)[1]
+    assert A.sector_dim(spec) == reps.shape[0]
+    np.testing.assert_array_equal(st, reps)
+
+
+@pytest.mark.parametrize("L,K,parity", [c for c in CASES if c[0] <= 17])
+def test_kernel_tables_reproduce_the_reduced_hamiltonian(L, K, parity):
+    Jxy, Jz = 0.7, 1.3
+    spec = A.SectorSpec(L, K, parity, Jxy=Jxy, Jz=Jz)
+    c = S.SectorChain(L, K, parity, Jxy, Jz, 1 | (1 << (L - 1)), 1.0)
+    rng = np.random.default_rng(L * 10 + K)
+    v = rng.standard_normal(c.D) + 1j * rng.standard_normal(c.D)
+    np.testing.assert_allclose(A.sector_apply_h0(spec, v), c.apply_H0(v), rtol=0, atol=1e-13 * np.abs(v).sum())
+
+
+def _status(fn, *args):
+    return fn(*args)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(L=1, K=0), _abi.KG_ERR_INVALID_ARG),
+    (dict(L=6, K=7), _abi.KG_ERR_INVALID_ARG),
+    (dict(L=6, K=2, parity=2), _abi.KG_ERR_INVALID_ARG),
+    (dict(L=6, K=2, hc_mask=0b000011), _abi.KG_ERR_INVALID_ARG),  # not mirror-symmetric
+    (dict(L=6, K=2, hc_mask=1 << 6), _abi.KG_ERR_INVALID_ARG),    # a site beyond L
+    (dict(L=22, K=11), _abi.KG_ERR_UNSUPPORTED),                  # too large for one CTA
+])
+def test_sector_argument_checks(kw, status):
+    spec = A.SectorSpec(**kw)
+    D = ctypes.c_int32(0)
+    assert _abi.lib().kg_sector_dim(ctypes.byref(spec.to_c()), ctypes.byref(D)) == status
+
+
+def test_asymmetric_mask_is_fine_without_parity():
+    assert A.sector_dim(A.SectorSpec(6, 2, 0, hc_mask=0b000011)) == 15
+
+
+@pytest.mark.parametrize("opts_kw,status", [
+    (dict(grad="exact"), _abi.KG_ERR_UNSUPPORTED),
+    (dict(ckpt_every=4), _abi.KG_ERR_UNSUPPORTED),
+    (dict(tile_bits=6), _abi.KG_ERR_INVALID_ARG),
+    (dict(host_staging=True), _abi.KG_ERR_INVALID_ARG),
+    (dict(phase_timing=True), _abi.KG_OK),
+    (dict(m=33), _abi.KG_ERR_INVALID_ARG),
+])
+def test_sector_option_checks(opts_kw, status):
+    spec = A.SectorSpec(10, 4, 1)
+    base = dict(N=16, dt=0.5, m=10)
+    base.update(opts_kw)
+    o = A.Options(**base)
+    n = ctypes.c_size_t(0)
+    assert _abi.lib().kg_sector_workspace_bytes(ctypes.byref(spec.to_c()), ctypes.byref(o.to_c()), 4,
+                                                ctypes.byref(n)) == status
+
+
+def test_sector_workspace_holds_a_trajectory_per_pulse():
+    spec = A.SectorSpec(10, 4, 1)
+    o = A.Options(N=440, dt=0.5, m=10, prec="c64")
+    one, four = A.sector_workspace_bytes(spec, o, 1), A.sector_workspace_bytes(spec, o, 4)
+    D = 110
+    assert one >= (440 + 1 + 10) * D * 8
+    assert four - one >= 3 * (440 + 1 + 10) * D * 8
+    o128 = A.Options(N=440, dt=0.5, m=10, prec="c128")
+    assert A.sector_workspace_bytes(spec, o128, 1) >= (440 + 1 + 10) * D * 16
+
+
+def test_sector_create_rejects_a_small_workspace():
+    spec = A.SectorSpec(10, 4, 1)
+    o = A.Options(N=16, dt=0.5, m=10)
+    h = ctypes.c_void_p(0)
+    st = _abi.lib().kg_sector_create(ctypes.byref(h), ctypes.byref(spec.to_c()), ctypes.byref(o.to_c()), 1,
+                                     ctypes.c_void_p(256), ctypes.c_size_t(1024), None)
+    assert st == _abi.KG_ERR_WORKSPACE

@@ -1,0 +1,165 @@
+"""GPU parity of the parity-excitation subspace kernel (Sec. 3.1) against the oracle's reduction.
+
+Same tolerances as the full chain: complex128 |dF|/F, ||dg||/||g|| <= 1e-10; complex64 + FP64
+recurrences 1e-5 / 1e-4.  The cases cover every block shape of the kernel (128 x 4, 256 x 4,
+256 x 8 and 512 x 8 rows), both parities and the whole sector, the three gradient modes, Lanczos
+breakdowns (D < m, D = 1), a batch larger than the grid, and the paper's L = 20, K = 4 subspace.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import oracle.sector as S
+from paper_2010_03598_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": (1e-10, 1e-10), "c64": (1e-5, 1e-4)}
+
+
+def api():
+    from paper_2010_03598_gb300 import api as A
+    return A
+
+
+@pytest.fixture(autouse=True, scope="module")
+def short_pulse_limit():
+    # 60 x 0.5 s = 30 s per pulse: a runaway pulse ends with KG_ERR_TIMEOUT well inside the test's time
+    A = api()
+    A.set_wait_limit_ns(500_000_000)
+    yield
+    A.set_wait_limit_ns(2_000_000_000)
+
+
+def nrel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def run(spec, opts, U, psi0, f, ctas=0):
+    A = api()
+    dev = torch.device("cuda", 0)
+    if ctas:
+        import dataclasses
+        opts = dataclasses.replace(opts, ctas=ctas)
+    eng = A.KGrapeSector(spec, opts, B=U.shape[0])
+    fid, grad = eng.evaluate(torch.tensor(U, device=dev), torch.tensor(psi0, device=dev),
+                             torch.tensor(f, device=dev))
+    rep = eng.sync()
+    out = fid.cpu().numpy().copy(), (grad.cpu().numpy().copy() if opts.grad != "none" else None), rep
+    eng.close()
+    return out
+
+
+def problem(L, K, parity, N, seed, target="last"):
+    c = S.paper_chain(L, K, parity)
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-1, 1, N)
+    psi0 = np.zeros(c.D, complex)
+    psi0[0] = 1.0
+    if target == "last":
+        f = np.zeros(c.D, complex)
+        f[-1] = 1.0
+    else:
+        f = rng.standard_normal(c.D) + 1j * rng.standard_normal(c.D)
+        f /= np.linalg.norm(f)
+    return c, u, psi0, f
+
+
+@pytest.mark.parametrize("L,K,parity,N,grad,prec,target", [
+    (10, 4, 1, 440, "centered", "c128", "last"),   # the paper's task e_1 -> e_D, M = 4D
+    (10, 4, 1, 440, "centered", "c64", "last"),
+    (8, 3, -1, 60, "zeroth", "c128", "random"),    # 128 x 4 block, odd parity
+    (9, 4, 0, 80, "centered", "c64", "random"),    # the whole K sector
+    (13, 6, 1, 50, "centered", "c128", "random"),  # D = 868: 256 x 4
+    (17, 4, 1, 30, "centered", "c64", "random"),   # D = 1204: 256 x 8
+    (17, 4, 1, 30, "zeroth", "c128", "random"),
+    (20, 4, 1, 24, "centered", "c64", "last"),     # D = 2445: 512 x 8
+    (20, 4, 1, 12, "centered", "c128", "random"),
+    (12, 6, -1, 40, "none", "c64", "random"),
+])
+def test_sector_vs_oracle(L, K, parity, N, grad, prec, target):
+    A = api()
+    c, u, psi0, f = problem(L, K, parity, N, seed=L * 1000 + K * 10 + parity + 1, target=target)
+    m, dt = 10, 0.5
+    F_ref, g_ref, d = oracle.evaluate(c, u, dt, m, psi0, f, grad)
+    fid, g, rep = run(A.SectorSpec(L, K, parity), A.Options(N, dt, m, prec=prec, grad=grad), u[None, :], psi0, f)
+    tf, tg = TOL[prec]
+    print(L, K, parity, prec, grad, "rel. err F", abs(fid[0] - F_ref) / abs(F_ref),
+          "grad", nrel(g[0], g_ref) if grad != "none" else None)
+    assert abs(fid[0] - F_ref) / abs(F_ref) <= tf, (fid[0], F_ref)
+    if grad != "none":
+        assert nrel(g[0], g_ref) <= tg, nrel(g[0], g_ref)
+    assert rep["breakdowns"] == 0
+    # ||psi_N||: FP32 rounding of the complex64 states walks by ~6e-8 per slice (sqrt(N) of it, x4 margin)
+    ntol = 1e-12 if prec == "c128" else 4 * 6e-8 * np.sqrt(N) + 1e-7
+    assert abs(rep["norm_final"] - np.linalg.norm(d["psi_N"])) <= ntol
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_sector_batch_larger_than_the_grid(prec):
+    # 5 pulses on 2 CTAs: CTA b takes pulses b, b + 2, b + 4 in turn, reusing its trajectory buffer
+    A = api()
+    L, K, N, dt, m = 9, 3, 60, 0.5, 10
+    c = S.paper_chain(L, K, 1)
+    rng = np.random.default_rng(5)
+    U = rng.uniform(-1, 1, (5, N))
+    psi0 = np.zeros(c.D, complex)
+    psi0[0] = 1.0
+    f = np.zeros(c.D, complex)
+    f[-1] = 1.0
+    fid, g, rep = run(A.SectorSpec(L, K, 1), A.Options(N, dt, m, prec=prec), U, psi0, f, ctas=2)
+    assert rep["ctas"] == 2
+    tf, tg = TOL[prec]
+    for b in range(5):
+        F_ref, g_ref, _ = oracle.evaluate(c, U[b], dt, m, psi0, f, "centered")
+        assert abs(fid[b] - F_ref) / F_ref <= tf
+        assert nrel(g[b], g_ref) <= tg
+
+
+@pytest.mark.parametrize("L,K,prec", [(3, 1, "c128"), (4, 2, "c64"), (6, 0, "c128")])
+def test_sector_breakdowns_match_the_oracle(L, K, prec):
+    # D = 2, 4, 1 < m: every slice's Lanczos basis ends early at an invariant subspace
+    A = api()
+    c, u, psi0, f = problem(L, K, 1, 20, seed=7, target="random")
+    F_ref, g_ref, d = oracle.evaluate(c, u, 0.5, 10, psi0, f, "centered")
+    fid, g, rep = run(A.SectorSpec(L, K, 1), A.Options(20, 0.5, 10, prec=prec), u[None, :], psi0, f)
+    tf, tg = TOL[prec]
+    assert abs(fid[0] - F_ref) <= tf * max(F_ref, 1e-3)
+    if np.linalg.norm(g_ref) > 1e-12:
+        assert nrel(g[0], g_ref) <= tg
+    else:
+        assert np.abs(g[0]).max() <= 1e-12
+    assert d["breakdowns_fwd"] + d["breakdowns_bwd"] == 40  # every slice of both sweeps
+    assert rep["breakdowns"] == 40
+
+
+def test_sector_equals_the_full_chain_kernel():
+    # The subspace kernel and the full 2^L kernel (embedded states) give one F and gradient.
+    A = api()
+    L, K, N, dt, m = 10, 3, 40, 0.5, 10
+    c, u, psi0, f = problem(L, K, 1, N, seed=11, target="random")
+    fid, g, _ = run(A.SectorSpec(L, K, 1), A.Options(N, dt, m, prec="c128"), u[None, :], psi0, f)
+    dev = torch.device("cuda", 0)
+    eng = A.KGrape(A.ChainSpec(L, c.Jxy, c.Jz, hc_kind="sz", hc_mask=c.hc_mask, hc_amp=c.hc_amp),
+                   A.Options(N, dt, m, prec="c128"))
+    Ff, gf = eng.evaluate(torch.tensor(u, device=dev), torch.tensor(c.embed(psi0), device=dev),
+                          torch.tensor(c.embed(f), device=dev))
+    eng.sync()
+    assert abs(fid[0] - float(Ff.item())) <= 1e-10 * fid[0]
+    assert nrel(g[0], gf.cpu().numpy()) <= 1e-10
+    eng.close()
+
+
+def test_papers_workload_at_full_size():
+    # pe_L20_K4 at its full N = 4D = 9780 slices: F and the whole gradient against the oracle
+    # (complex128 oracle, one pulse; complex64 kernel, the benchmark's block shape)
+    A = api()
+    w = W.SECTOR_WORKLOADS["pe_L20_K4"]
+    c = S.paper_chain(w.L, w.K)
+    U, psi0, f = W.sector_instance(w, c.D, batch=1)
+    F_ref, g_ref, _ = oracle.evaluate(c, U[0], w.dt, w.m, psi0, f, "centered")
+    fid, g, rep = run(A.SectorSpec(w.L, w.K, w.parity), A.Options(U.shape[1], w.dt, w.m, prec="c64"), U, psi0, f)
+    print("pe_L20_K4 full size: rel. err F", abs(fid[0] - F_ref) / F_ref, "grad", nrel(g[0], g_ref))
+    assert abs(fid[0] - F_ref) / F_ref <= 1e-4
+    assert nrel(g[0], g_ref) <= 1e-3
