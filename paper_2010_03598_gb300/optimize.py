@@ -127,7 +127,8 @@ def lbfgs_maximize_fidelity(fun: FidelityAndGradient, u0: np.ndarray, *, target_
 
 
 class PulseObjective:
-    """F and dF/du of a pulse through a ``KGrape`` engine (one library evaluation per call).
+    """F and dF/du of a pulse through a ``KGrape`` engine, or a ``KGrapeSector`` engine created
+    for one pulse (one library evaluation per call).
 
     The initial and target states stay on the device; each call copies the N controls in,
     runs one evaluation and reads F and the gradient back.
@@ -136,15 +137,19 @@ class PulseObjective:
     def __init__(self, engine, psi0, target):
         import torch
 
+        batch = getattr(engine, "B", None)
+        if batch not in (None, 1):
+            raise ValueError("PulseObjective drives one pulse: create the subspace engine with B = 1")
         self.engine = engine
         self.psi0 = psi0
         self.target = target
-        self.u = torch.empty(engine.opts.N, dtype=torch.float64, device=psi0.device)
+        shape = (engine.opts.N,) if batch is None else (1, engine.opts.N)
+        self.u = torch.empty(shape, dtype=torch.float64, device=psi0.device)
 
     def __call__(self, u: np.ndarray):
         import torch
 
-        self.u.copy_(torch.as_tensor(u, dtype=torch.float64))
+        self.u.copy_(torch.as_tensor(u, dtype=torch.float64).reshape(self.u.shape))
         fid, grad = self.engine.evaluate(self.u, self.psi0, self.target)
         self.engine.sync()
-        return float(fid.item()), grad.cpu().numpy().copy()
+        return float(fid.reshape(-1)[0].item()), grad.reshape(-1).cpu().numpy().copy()

@@ -64,3 +64,29 @@ def test_library_driven_optimisation_follows_the_oracle(prec):
         # complex128 agrees with the oracle to ~1e-14: the first steps are the oracle's
         n = min(10, len(r.history), len(ref.history))
         np.testing.assert_allclose(r.history[:n], ref.history[:n], rtol=0, atol=1e-9)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_papers_transfer_task_is_optimised_on_the_gpu(prec):
+    # Sec. 3.2: e_1 -> e_D in the even-parity subspace of K = 2 excitations on L = 9 sites (D = 20),
+    # M = 4D = 80 controls from U(-1, 1), dt = 0.5, m = 10, stop at I <= 1e-2 (no traps, as the paper
+    # reports for these settings)
+    import torch
+    import oracle.sector as S
+    from paper_2010_03598_gb300 import api as A
+
+    w = W.SectorWorkload("pe_L9_K2", L=9, K=2)
+    c = S.paper_chain(w.L, w.K)
+    U, psi0, f = W.sector_instance(w, c.D)
+    ref = lbfgs_maximize_fidelity(lambda u: oracle.evaluate(c, u, w.dt, w.m, psi0, f, "centered")[:2], U[0],
+                                  max_iter=300)
+    dev = torch.device("cuda", 0)
+    eng = A.KGrapeSector(A.SectorSpec(w.L, w.K, w.parity), A.Options(U.shape[1], w.dt, w.m, prec=prec), B=1)
+    obj = PulseObjective(eng, torch.tensor(psi0, device=dev), torch.tensor(f, device=dev))
+    r = lbfgs_maximize_fidelity(obj, U[0], max_iter=300)
+    eng.close()
+    assert ref.reason == "target" and r.reason == "target" and r.F >= 0.99
+    if prec == "c128":
+        n = min(10, len(r.history), len(ref.history))
+        np.testing.assert_allclose(r.history[:n], ref.history[:n], rtol=0, atol=1e-9)
