@@ -27,6 +27,12 @@ propagator of Appendix A:
   1/12, 5/12, 5/12, 1/12 (exact for polynomials of degree 5).  The end nodes are
   G_{j-1} and G_j; the interior states are Krylov steps of psi_{j-1} and chi_j over
   the partial lengths.
+* Taylor hierarchy (App. B, Eq. gradp): the slice average of the control operator,
+  Hbar_c = (1/dt) int_0^dt e^{-i tau H_j} Hc e^{+i tau H_j} dtau, expanded in the Liouvillian
+  L = [H_j, .]: Hbar_c^[P] = sum_{p<=P} (-i dt)^p / (p+1)! L^p Hc, and
+  dF/du_{j-1} ~ 2 dt Im <chi_j| Hbar_c^[P] |psi_j>.  P = 0 is the zeroth-order gradient.
+  (L^p Hc) x is formed by its recursive definition, (L^p Hc) x = H (L^{p-1} Hc) x -
+  (L^{p-1} Hc) H x.  Grad modes "taylor1" .. "taylor6".
 
 Returned gradients are of the fidelity F (= -dI/du).
 """
@@ -37,7 +43,7 @@ import numpy as np
 from .chain import Chain
 from .krylov import DEFAULT_BREAKDOWN_TOL, krylov_step
 
-GRAD_MODES = ("none", "centered", "zeroth", "exact")
+GRAD_MODES = ("none", "centered", "zeroth", "exact", "taylor1", "taylor2", "taylor3", "taylor4", "taylor5", "taylor6")
 
 
 def forward(chain: Chain, u: np.ndarray, dt: float, m: int, psi0: np.ndarray,
@@ -94,6 +100,8 @@ def evaluate(chain: Chain, u: np.ndarray, dt: float, m: int, psi0: np.ndarray,
     diag.update(G=G, chi_0=chi, err_bwd=berr, breakdowns_bwd=bbrk)
     if grad_mode == "zeroth":
         grad = G[1:].copy()
+    elif grad_mode.startswith("taylor"):
+        grad = taylor_gradient(chain, u, dt, m, psis, beta * target, int(grad_mode[6:]), tol)
     elif grad_mode == "exact":
         Gi = lobatto_interior(chain, u, dt, m, psis, beta * target, tol)
         diag.update(G_interior=Gi)
@@ -130,6 +138,36 @@ def lobatto_interior(chain: Chain, u: np.ndarray, dt: float, m: int, psis, chi_N
             Gi[j - 1, a] = overlaps_G(chain, dt, chi_s, psi_s)
         chi, _ = krylov_step(Hj, chi, dt, m, -1, tol)
     return Gi
+
+
+def liouvillian_power_hc(apply_H, apply_Hc, p: int, x: np.ndarray) -> np.ndarray:
+    """(L^p Hc) x with L = [H, .], by the definition L^p Hc = H (L^{p-1} Hc) - (L^{p-1} Hc) H."""
+    if p == 0:
+        return apply_Hc(x)
+    return apply_H(liouvillian_power_hc(apply_H, apply_Hc, p - 1, x)) - \
+        liouvillian_power_hc(apply_H, apply_Hc, p - 1, apply_H(x))
+
+
+def taylor_gradient(chain: Chain, u: np.ndarray, dt: float, m: int, psis, chi_N: np.ndarray, P: int,
+                    tol: float = DEFAULT_BREAKDOWN_TOL) -> np.ndarray:
+    """dF/du_{j-1} ~ 2 dt Im <chi_j| Hbar_c^[P] |psi_j>, j = 1..N (App. B, Eq. gradp).
+
+    chi_j is propagated back slice by slice as in ``evaluate``; H = H_j inside slice j.
+    """
+    from math import factorial
+
+    N = len(u)
+    grad = np.zeros(N)
+    chi = np.asarray(chi_N, dtype=np.complex128)
+    for j in range(N, 0, -1):
+        uj = float(u[j - 1])
+        Hj = lambda v, uj=uj: chain.apply_H(uj, v)
+        acc = 0j
+        for p in range(P + 1):
+            acc += (-1j * dt) ** p / factorial(p + 1) * np.vdot(chi, liouvillian_power_hc(Hj, chain.apply_Hc, p, psis[j]))
+        grad[j - 1] = 2.0 * dt * acc.imag
+        chi, _ = krylov_step(Hj, chi, dt, m, -1, tol)
+    return grad
 
 
 def segment_forward_backward(chain: Chain, u: np.ndarray, dt: float, m: int,

@@ -356,3 +356,42 @@ def test_lobatto_gradient_matches_the_dense_derivative(L):
     err_c = np.linalg.norm(g_c - g_ex) / np.linalg.norm(g_ex)
     assert err_l <= 1e-8 and err_l <= 1e-4 * err_c, (err_l, err_c)
     assert d["G_interior"].shape == (N, 2)
+
+
+@pytest.mark.parametrize("mode,Ns,lo,hi", [("taylor1", [16, 32, 64], 6.8, 9.2),    # O(dt^3)
+                                           ("taylor2", [8, 16, 32], 13.5, 18.5),   # O(dt^4)
+                                           ("taylor3", [8, 16, 32], 26.0, 36.0)])  # O(dt^5)
+def test_taylor_hierarchy_error_orders(mode, Ns, lo, hi):
+    # App. B, Eq. gradp: each level p of Hbar_c^[P] adds one order in dt to the slice average of
+    # the control operator, so the gradient error falls as dt^(P+2).
+    errs = _grad_errors(mode, Ns)
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(lo < r < hi for r in ratios), (errs, ratios)
+
+
+def test_taylor_level_zero_is_the_zeroth_order_gradient():
+    from oracle.grape import taylor_gradient
+    rng = np.random.default_rng(4)
+    L, N, dt = 4, 10, 0.1
+    ch = oracle.Chain(L, 1.0, 0.5)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    F, g0, d = oracle.evaluate(ch, u, dt, 14, psi0, f, "zeroth")
+    psis, _ = oracle.forward(ch, u, dt, 14, psi0)
+    gt = taylor_gradient(ch, u, dt, 14, psis, d["beta"] * f, 0)
+    np.testing.assert_allclose(gt, g0, rtol=0, atol=1e-14)
+
+
+def test_taylor_hierarchy_converges_to_the_dense_derivative():
+    # Hbar_c^[P] is a convergent series: at P = 6 and dt = 0.1 the gradient equals the exact
+    # propagator derivative (divided differences, an independent route) to ~1e-9.
+    rng = np.random.default_rng(12)
+    L, N, dt = 5, 6, 0.1
+    ch = oracle.Chain(L, 1.0, 0.5)
+    u = rng.uniform(-1, 1, N)
+    f = W.draw_target(rng, 1 << L)
+    psi0 = W.neel_state(L)
+    _, g_ex = oracle.exact_gradient(ch, u, dt, psi0, f)
+    _, g6, _ = oracle.evaluate(ch, u, dt, 16, psi0, f, "taylor6")
+    assert np.linalg.norm(g6 - g_ex) / np.linalg.norm(g_ex) < 1e-9
