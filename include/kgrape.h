@@ -61,13 +61,21 @@ typedef enum kg_grad_mode {
   KG_GRAD_NONE = 0,        /* fidelity only (no backward sweep) */
   KG_GRAD_CENTERED = 1,    /* (G_{j-1} + G_j) / 2, the gradient fed to L-BFGS in Sec. 2 */
   KG_GRAD_ZEROTH = 2,      /* G_j (Eq. gradI) */
-  KG_GRAD_EXACT = 3        /* the natural gradient G(t) = 2 dt Im <chi(t)|Hc|psi(t)> averaged over
+  KG_GRAD_EXACT = 3,       /* the natural gradient G(t) = 2 dt Im <chi(t)|Hc|psi(t)> averaged over
                               slice j (App. B, Eqs. natu_integr, natgrad) with the 4-point
                               Gauss-Lobatto rule: nodes t_{j-1} + s, s = 0, (1 -+ 1/sqrt 5) dt/2, dt,
                               weights 1/12, 5/12, 5/12, 1/12; exact up to O(dt^7) per component.
                               The interior states come from the slices' own Krylov bases (two more
                               recombinations per slice and direction); the workspace keeps 2N more
                               vectors.  Not combined with checkpointing (KG_ERR_UNSUPPORTED). */
+  KG_GRAD_TAYLOR1 = 4,     /* 2 dt Im <chi_j| Hbar_c^[P] |psi_j> with the slice average of Hc expanded in
+                              the Liouvillian L = [H_j, .] (App. B, Eq. gradp):
+                              Hbar_c^[P] = sum_{p<=P} (-i dt)^p/(p+1)! L^p Hc, here P = 1 (error
+                              O(dt^3) per component; P = 0 would be KG_GRAD_ZEROTH) */
+  KG_GRAD_TAYLOR2 = 5      /* the same with P = 2 (error O(dt^4)).  Both Taylor modes are available for
+                              parity-excitation subspaces (kg_sector_*), where H_j chi_j and H_j^2 chi_j
+                              come from the slice's Lanczos vectors and H_j psi_j, H_j^2 psi_j from one or
+                              two extra applications of H_j; kg_create answers KG_ERR_UNSUPPORTED */
 } kg_grad_mode;
 
 typedef enum kg_hc_kind {
@@ -294,7 +302,8 @@ kg_status kg_sector_states(const kg_sector* sector, uint64_t* states, int32_t D)
  * - 2 popcount(s_r & mask)) on row r. */
 kg_status kg_sector_apply_h0(const kg_sector* sector, const double* v, double* w, int32_t D);
 
-/* Workspace bytes for B pulses with options opts (N, m <= 32, prec, grad NONE / CENTERED / ZEROTH,
+/* Workspace bytes for B pulses with options opts (N, m <= 32, prec, grad NONE / CENTERED / ZEROTH /
+ * TAYLOR1 / TAYLOR2,
  * dt, breakdown_tol, ctas = most CTAs to use (0 = every one that fits); ckpt_every and tile_bits
  * must be 0; flags: KG_FLAG_PHASE_TIMING only, recording CTA 0's cycles in kg_report.phase_cycles as
  * [0] Lanczos gathers and updates, [1] block reductions, [4] tridiagonal T and small exponential,

@@ -11,7 +11,7 @@ KG_OK, KG_ERR_INVALID_ARG, KG_ERR_UNSUPPORTED, KG_ERR_CUDA, KG_ERR_NONFINITE, KG
 STATUS_NAMES = {0: "KG_OK", 1: "KG_ERR_INVALID_ARG", 2: "KG_ERR_UNSUPPORTED", 3: "KG_ERR_CUDA",
                 4: "KG_ERR_NONFINITE", 5: "KG_ERR_TIMEOUT", 6: "KG_ERR_WORKSPACE"}
 KG_PREC_C128, KG_PREC_C64_F64REC = 0, 1
-KG_GRAD_NONE, KG_GRAD_CENTERED, KG_GRAD_ZEROTH, KG_GRAD_EXACT = 0, 1, 2, 3
+KG_GRAD_NONE, KG_GRAD_CENTERED, KG_GRAD_ZEROTH, KG_GRAD_EXACT, KG_GRAD_TAYLOR1, KG_GRAD_TAYLOR2 = 0, 1, 2, 3, 4, 5
 KG_HC_SX_SITE, KG_HC_SZ_SITES = 0, 1
 KG_FLAG_HOST_STAGING = 1
 KG_FLAG_PHASE_TIMING = 2

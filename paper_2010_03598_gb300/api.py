@@ -15,7 +15,7 @@ from ._abi import check, lib
 
 _PREC = {"c128": _abi.KG_PREC_C128, "c64": _abi.KG_PREC_C64_F64REC}
 _GRAD = {"none": _abi.KG_GRAD_NONE, "centered": _abi.KG_GRAD_CENTERED, "zeroth": _abi.KG_GRAD_ZEROTH,
-         "exact": _abi.KG_GRAD_EXACT}
+         "exact": _abi.KG_GRAD_EXACT, "taylor1": _abi.KG_GRAD_TAYLOR1, "taylor2": _abi.KG_GRAD_TAYLOR2}
 
 
 @dataclasses.dataclass(frozen=True)
@@ -43,7 +43,8 @@ class Options:
     dt: float
     m: int
     prec: str = "c64"         # "c64" (complex64 state, FP64 recurrences) or "c128"
-    grad: str = "centered"    # "none", "centered", "zeroth", "exact" (Gauss-Lobatto over each slice)
+    grad: str = "centered"    # "none", "centered", "zeroth", "exact" (Gauss-Lobatto over each slice),
+                              # "taylor1", "taylor2" (App. B's hierarchy; subspace engines only)
     ckpt_every: int = 0
     tile_bits: int = 0
     ctas: int = 0

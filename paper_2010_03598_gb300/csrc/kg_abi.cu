@@ -57,6 +57,8 @@ kg_status check_args(const kg_chain* ch, const kg_options* o) {
   if (o->m < 1 || o->m > kg::kMaxM) return fail(KG_ERR_INVALID_ARG, "m must satisfy 1 <= m <= 32");
   if (o->prec != KG_PREC_C128 && o->prec != KG_PREC_C64_F64REC)
     return fail(KG_ERR_INVALID_ARG, "prec must be KG_PREC_C128 or KG_PREC_C64_F64REC");
+  if (o->grad == KG_GRAD_TAYLOR1 || o->grad == KG_GRAD_TAYLOR2)
+    return fail(KG_ERR_UNSUPPORTED, "Taylor-hierarchy gradients are available for subspaces (kg_sector_*)");
   if (o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED && o->grad != KG_GRAD_ZEROTH &&
       o->grad != KG_GRAD_EXACT)
     return fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, _CENTERED, _ZEROTH or _EXACT");

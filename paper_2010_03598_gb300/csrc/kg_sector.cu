@@ -86,7 +86,7 @@ struct SecSmem {
   float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
   float coef_f[2][kMaxM];
   double coef_d[2][kMaxM];
-  double beta_m, nrm_d, ex_d, err_max;
+  double beta_m, nrm_d, ex_d, tay_d, err_max;
   float beta_m_f, inv_f;
   unsigned ff_e_set;
   int breakdowns;
@@ -186,6 +186,109 @@ __device__ __forceinline__ SecStep sec_scalars(const FF (&o)[3], bool last, FF& 
   return s;
 }
 
+// Taylor-hierarchy terms of backward slice j (App. B, Eq. gradp), this thread's partial sum:
+// x was chi_j, psi_end is psi_j, H = H_j, and Im <chi| Hbar_c^[P] |psi> with a_m = H^m chi,
+// b_n = H^n psi and Hc diagonal is
+//   P = 1: Im M00 - (dt/2) Re(M10 - M01);  P = 2: also - (dt^2/6) Im(M20 - 2 M11 + M02),
+// M_mn = <a_m|Hc|b_n>.  The a_m come from the slice's Lanczos vectors (H v_0 = alpha_0 v_0 +
+// b_1 v_1, H v_1 = b_1 v_0 + alpha_1 v_1 + b_2 v_2), the b_n from the slice's gather applied to
+// psi_j once or twice.  Nothing reads the shared vectors after the Lanczos loop.  Kept out of
+// line: it runs once per backward slice and its arrays would crowd the Lanczos loop's registers.
+template <class V, int NT, int RPT>
+__device__ __noinline__ typename VecTraits<V>::R sec_taylor(const SectorParams& p, SecSmem& sm, V* Sa, V* Sb,
+                                                          const unsigned short* ell, const V* basis, double uj,
+                                                          int meff, typename VecTraits<V>::R nin, int taylor,
+                                                          const V* psi_end) {
+  using R = typename VecTraits<V>::R;
+  constexpr bool F32 = sizeof(R) == 4;
+  const int tid = threadIdx.x, D = p.D, ne = p.ell;
+  const R* wcls = F32 ? (const R*)sm.wcls_f : (const R*)sm.wcls_d;
+  // the diagonals of H0 and Hc, formed again here from the rows' states (as in sec_eval)
+  R dj[RPT], hh[RPT];
+  const int npc = __popc(p.hc_mask);
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int r = tid + NT * i;
+    dj[i] = 0;
+    hh[i] = 0;
+    if (r < D) {
+      const unsigned st = p.states[r];
+      const R d0 = (R)(p.qz * (double)(p.L1 - 2 * __popc((st ^ (st >> 1)) & p.maskL1)));
+      hh[i] = (R)(0.5 * p.hc_amp * (double)(npc - 2 * __popc(st & p.hc_mask)));
+      dj[i] = fma((R)uj, hh[i], d0);
+    }
+  }
+  R pt = 0;
+  V b0[RPT], b1[RPT], b2[RPT];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int r = tid + NT * i;
+    b0[i] = (r < D) ? psi_end[r] : vmake<V>(0, 0);
+    b2[i] = vmake<V>(0, 0);
+    if (r < D) Sa[r] = b0[i];
+  }
+  sec_sync();
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int r = tid + NT * i;
+    V h = vmake<V>(0, 0);
+    if (r < D) {
+      h = vscale<V>(dj[i], b0[i]);
+#pragma unroll 4
+      for (int e = 0; e < ne; ++e) {
+        const unsigned en = ell[e * D + r];
+        h = vaxpy<V>(wcls[en >> kSecColBits], Sa[en & (kSecMaxD - 1)], h);
+      }
+      if (taylor >= 2) Sb[r] = h;
+    }
+    b1[i] = h;
+  }
+  if (taylor >= 2) {
+    sec_sync();
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = tid + NT * i;
+      if (r < D) {
+        V h = vscale<V>(dj[i], b1[i]);
+#pragma unroll 4
+        for (int e = 0; e < ne; ++e) {
+          const unsigned en = ell[e * D + r];
+          h = vaxpy<V>(wcls[en >> kSecColBits], Sb[en & (kSecMaxD - 1)], h);
+        }
+        b2[i] = h;
+      }
+    }
+  }
+  const R al0 = (meff > 0) ? (F32 ? (R)sm.alpha_f[0] : (R)sm.alpha[0]) : (R)0;
+  const R al1 = (meff > 1) ? (F32 ? (R)sm.alpha_f[1] : (R)sm.alpha[1]) : (R)0;
+  const R be1 = (meff > 1) ? (F32 ? (R)sm.beta_f[1] : (R)sm.beta[1]) : (R)0;
+  const R be2 = (meff > 2) ? (F32 ? (R)sm.beta_f[2] : (R)sm.beta[2]) : (R)0;
+  const R c0 = al0 * al0 + be1 * be1, c1 = be1 * (al0 + al1), c2 = be1 * be2;
+  const R h1 = (R)(0.5 * p.dt), h2 = (R)(p.dt * p.dt / 6.0);
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int r = tid + NT * i;
+    if (r < D && meff > 0) {
+      const V v0 = basis[r];
+      const V v1 = (meff > 1) ? basis[(size_t)D + r] : vmake<V>(0, 0);
+      const V v2 = (taylor >= 2 && meff > 2) ? basis[(size_t)2 * D + r] : vmake<V>(0, 0);
+      const V a0 = vscale<V>(nin, v0);
+      const V a1 = vscale<V>(nin, vaxpy<V>(be1, v1, vscale<V>(al0, v0)));
+      // conj(a) b = (a.x b.x + a.y b.y) + i (a.x b.y - a.y b.x)
+      R t = a0.x * b0[i].y - a0.y * b0[i].x;                                                   // Im M00
+      t -= h1 * ((a1.x * b0[i].x + a1.y * b0[i].y) - (a0.x * b1[i].x + a0.y * b1[i].y));     // Re(M10 - M01)
+      if (taylor >= 2) {
+        const V a2 = vscale<V>(nin, vaxpy<V>(c2, v2, vaxpy<V>(c1, v1, vscale<V>(c0, v0))));
+        const R i20 = a2.x * b0[i].y - a2.y * b0[i].x, i11 = a1.x * b1[i].y - a1.y * b1[i].x;
+        const R i02 = a0.x * b2[i].y - a0.y * b2[i].x;
+        t -= h2 * (i20 - (R)2 * i11 + i02);
+      }
+      pt = fma(hh[i], t, pt);
+    }
+  }
+  return pt;
+}
+
 // One slice: x (own rows, norm nrm) -> x = ||x|| V exp(-i tau T) e_1 (App. A), written to dst
 // (if not null), then ||x||^2 and, for extra = 1, G = Im <x| Hc |other> over the own rows are
 // reduced.  Returns false after a non-finite coefficient (status set).
@@ -195,7 +298,8 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
                                           const typename VecTraits<V>::R (&dd)[RPT],
                                           const typename VecTraits<V>::R (&hh)[RPT], double uj, double tau,
                                           V (&x)[RPT], double& nrm, typename VecTraits<V>::R& inv, int extra,
-                                          const V* other, V* dst, double& ex) {
+                                          const V* other, V* dst, double& ex, int taylor = 0,
+                                          const V* psi_end = nullptr, double* tay = nullptr) {
   using R = typename VecTraits<V>::R;
   constexpr bool F32 = sizeof(R) == 4;
   const int tid = threadIdx.x, D = p.D, m = p.m, ne = p.ell;
@@ -205,6 +309,7 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
   for (int i = 0; i < RPT; ++i) dj[i] = fma((R)uj, hh[i], dd[i]);
   // ---- v_0 = x / ||x||
   const R inv0 = inv;
+  const R nin = (R)nrm;  // ||x||: the Taylor terms rebuild H x, H^2 x from the basis
   V* Sc = Sa;
   V* Sn = Sb;
 #pragma unroll
@@ -459,11 +564,14 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
     }
     x[i] = y[i];
   }
+  // ---- Taylor hierarchy (App. B, Eq. gradp), backward slice j (sec_taylor)
+  R pt = 0;
+  if (taylor > 0) pt = sec_taylor<V, NT, RPT>(p, sm, Sa, Sb, ell, basis, uj, meff, nin, taylor, psi_end);
   if constexpr (F32) {
-    const float vals[2] = {pn, pg};
-    FF o[2];
+    const float vals[3] = {pn, pg, pt};
+    FF o[3];
     sec_mark(p, sm, 5);
-    sec_reduce<NT, 2>(sm, par, vals, o);
+    sec_reduce<NT, 3>(sm, par, vals, o);
     if (!isfinite(o[0].hi)) {
       if (tid == 0) {
         sec_flag(p, KG_ERR_NONFINITE);
@@ -478,16 +586,18 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
       sm.nrm_d = n;
       sm.inv_f = (n > 0.0) ? (float)(1.0 / n) : 0.f;
       sm.ex_d = (extra == 1) ? ff_to_double(o[1]) : 0.0;
+      sm.tay_d = (taylor > 0) ? ff_to_double(o[2]) : 0.0;
     }
     sec_sync();
     nrm = sm.nrm_d;
     inv = (R)sm.inv_f;
     ex = sm.ex_d;
+    if (tay) *tay = sm.tay_d;
   } else {
-    const double vals[2] = {pn, pg};
-    double o[2];
+    const double vals[3] = {pn, pg, pt};
+    double o[3];
     sec_mark(p, sm, 5);
-    sec_reduce<NT, 2>(sm, par, vals, o);
+    sec_reduce<NT, 3>(sm, par, vals, o);
     if (!isfinite(o[0])) {
       if (tid == 0) {
         sec_flag(p, KG_ERR_NONFINITE);
@@ -498,6 +608,7 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
     nrm = sqrt(fmax(o[0], 0.0));
     inv = (nrm > 0.0) ? (R)(1.0 / nrm) : (R)0;
     ex = o[1];
+    if (tay) *tay = o[2];
   }
   sec_mark(p, sm, 1);
   return true;
@@ -603,6 +714,7 @@ __device__ __forceinline__ void sec_eval(const SectorParams& p, int b, SecSmem& 
     bi = o[1];
   }
   if (p.grad_mode != KG_GRAD_NONE) {
+    const int taylor = (p.grad_mode == KG_GRAD_TAYLOR1) ? 1 : (p.grad_mode == KG_GRAD_TAYLOR2) ? 2 : 0;
     // chi_N = beta f; G_N = 2 dt Im <chi_N|Hc|psi_N>
     double acc[2] = {0.0, 0.0};
 #pragma unroll
@@ -626,17 +738,21 @@ __device__ __forceinline__ void sec_eval(const SectorParams& p, int b, SecSmem& 
     sec_mark(p, sm, 6);
     for (int j = N; j >= 1; --j) {
       // chi_{j-1} = exp(+i dt H_j) chi_j, fused G_{j-1} = 2 dt Im <chi_{j-1}|Hc|psi_{j-1}>
+      double tay = 0.0;
       if (!sec_slice<V, NT, RPT>(p, sm, par, S0, S1, ell, basis, dd, hh, u[j - 1], -p.dt, x, nrm, inv, 1,
-                                 traj + (size_t)(j - 1) * D, nullptr, ex)) {
+                                 traj + (size_t)(j - 1) * D, nullptr, ex, taylor, traj + (size_t)j * D, &tay)) {
         if (tid == 0) sec_abandon(p, sm, b, -j);
         return;
       }
-      if (tid == 0) G[j - 1] = 2.0 * p.dt * ex;
+      if (tid == 0) {
+        G[j - 1] = 2.0 * p.dt * ex;
+        if (taylor) G[j] = 2.0 * p.dt * tay;  // slice j's Taylor-hierarchy value replaces G_j
+      }
     }
     sec_sync();  // G complete (written by thread 0)
     double* gb = p.grad + (size_t)b * N;
     for (int j = tid; j < N; j += NT)
-      gb[j] = (p.grad_mode == KG_GRAD_CENTERED) ? 0.5 * (G[j] + G[j + 1]) : G[j + 1];
+      gb[j] = (p.grad_mode == KG_GRAD_CENTERED) ? 0.5 * (G[j] + G[j + 1]) : G[j + 1];  // zeroth, Taylor
   }
   if (tid == 0) {
     p.fid[b] = br * br + bi * bi;
@@ -651,8 +767,10 @@ __device__ __forceinline__ void sec_eval(const SectorParams& p, int b, SecSmem& 
   sec_sync();
 }
 
+// Blocks of up to 256 threads are held to 128 registers a thread, so that two CTAs (two pulses)
+// share an SM and hide each other's barrier and FP64 latency.
 template <class V, int NT, int RPT>
-__global__ void __launch_bounds__(NT) kg_sector_kernel(const __grid_constant__ SectorParams p) {
+__global__ void __launch_bounds__(NT, (NT <= 256) ? 2 : 1) kg_sector_kernel(const __grid_constant__ SectorParams p) {
   extern __shared__ __align__(16) unsigned char sec_dyn[];
   __shared__ SecSmem sm;
   const int Dp = (p.D + 15) & ~15;
@@ -877,8 +995,9 @@ kg_status check_sector_opts(const kg_options* o, int B) {
   if (o->prec != KG_PREC_C128 && o->prec != KG_PREC_C64_F64REC)
     return host_fail(KG_ERR_INVALID_ARG, "prec must be KG_PREC_C128 or KG_PREC_C64_F64REC");
   if (o->grad == KG_GRAD_EXACT) return host_fail(KG_ERR_UNSUPPORTED, "KG_GRAD_EXACT is not available for subspaces");
-  if (o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED && o->grad != KG_GRAD_ZEROTH)
-    return host_fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, _CENTERED or _ZEROTH");
+  if (o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED && o->grad != KG_GRAD_ZEROTH &&
+      o->grad != KG_GRAD_TAYLOR1 && o->grad != KG_GRAD_TAYLOR2)
+    return host_fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, _CENTERED, _ZEROTH, _TAYLOR1 or _TAYLOR2");
   if (o->ckpt_every != 0) return host_fail(KG_ERR_UNSUPPORTED, "subspace evaluations keep every state: ckpt_every must be 0");
   if (o->tile_bits != 0) return host_fail(KG_ERR_INVALID_ARG, "tile_bits must be 0 for subspaces");
   if ((o->flags & ~KG_FLAG_PHASE_TIMING) != 0)

@@ -56,6 +56,8 @@ def test_asymmetric_mask_is_fine_without_parity():
 
 @pytest.mark.parametrize("opts_kw,status", [
     (dict(grad="exact"), _abi.KG_ERR_UNSUPPORTED),
+    (dict(grad="taylor1"), _abi.KG_OK),
+    (dict(grad="taylor2"), _abi.KG_OK),
     (dict(ckpt_every=4), _abi.KG_ERR_UNSUPPORTED),
     (dict(tile_bits=6), _abi.KG_ERR_INVALID_ARG),
     (dict(host_staging=True), _abi.KG_ERR_INVALID_ARG),
@@ -90,3 +92,12 @@ def test_sector_create_rejects_a_small_workspace():
     st = _abi.lib().kg_sector_create(ctypes.byref(h), ctypes.byref(spec.to_c()), ctypes.byref(o.to_c()), 1,
                                      ctypes.c_void_p(256), ctypes.c_size_t(1024), None)
     assert st == _abi.KG_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("grad", ["taylor1", "taylor2"])
+def test_full_chain_refuses_taylor_gradients(grad):
+    ch = A.ChainSpec(8, 1.0, 0.5)
+    o = A.Options(N=16, dt=0.05, m=10, grad=grad)
+    n = ctypes.c_size_t(0)
+    assert _abi.lib().kg_workspace_bytes(ctypes.byref(ch.to_c()), ctypes.byref(o.to_c()),
+                                         ctypes.byref(n)) == _abi.KG_ERR_UNSUPPORTED
