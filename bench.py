@@ -162,6 +162,33 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ---------------------------------------------------------------- replicas (one process per GPU)
+def replica_sync(world: int, device):
+    """(barrier, max_over_ranks) for independent replicas: the evaluation does not shard, so the
+    only collectives are the barrier around the timed region and the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return barrier, max_over_ranks
+
+
+def job_throughput(units_per_rank: int, seconds_this_rank: float, world: int, max_over_ranks):
+    """Whole-job value: every rank processed units_per_rank; the job took the slowest rank's time."""
+    t = max_over_ranks(seconds_this_rank)
+    return units_per_rank * world / t, t
+
+
 # ---------------------------------------------------------------- CPU oracle sample
 ORACLE_SNIPPET = r"""
 import json, sys, time
@@ -255,16 +282,7 @@ def run_ours(args):
     from paper_2010_03598_gb300 import api as A
     W, w = workload(args.workload, args.N)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = replica_sync(world, dev)
 
     u, psi0, f = W.instance(w)
     ut = torch.tensor(u, device=dev)
@@ -311,8 +329,7 @@ def run_ours(args):
     sampler.start()
     ms, rep, fid, wall = timed(args.prec, args.steps, args.warmup)
     clocks = sampler.stop()
-    total_s = max_over_ranks(sum(ms) / 1e3)
-    value = args.steps * world / total_s
+    value, total_s = job_throughput(args.steps, sum(ms) / 1e3, world, max_over_ranks)
     ms_per_step = total_s * 1e3 / args.steps
     hbm, peak_kind = measured_peaks()
     per_launch_s = statistics.mean(ms) / 1e3
