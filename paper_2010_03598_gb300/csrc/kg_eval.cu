@@ -727,7 +727,10 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
     __syncthreads();  // every thread is done with the Lanczos loop's shared memory
     if (tid >= 32) {  // warp 0 issues its copies after the exponential
       for (int s = 0; s < kRecombDepth; ++s) {
-        if (s < meff) recomb_issue(s == 0 ? src : c.basis_slot(s), rb, c.n_own, stg + (size_t)s * 8 * kThreads);
+        if (s < meff) {  // newest basis vector first (see the loop below)
+          const int ks = meff - 1 - s;
+          recomb_issue(ks == 0 ? src : c.basis_slot(ks), rb, c.n_own, stg + (size_t)s * 8 * kThreads);
+        }
         cp_async_commit();
       }
     }
@@ -786,7 +789,10 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
         ss.coef_im_f[0] -= ei * al * ss.f_ib0;
       }
       for (int s = 0; s < kRecombDepth; ++s) {
-        if (s < meff) recomb_issue(s == 0 ? src : c.basis_slot(s), rb, c.n_own, stg + (size_t)s * 8 * kThreads);
+        if (s < meff) {  // newest basis vector first (see the loop below)
+          const int ks = meff - 1 - s;
+          recomb_issue(ks == 0 ? src : c.basis_slot(ks), rb, c.n_own, stg + (size_t)s * 8 * kThreads);
+        }
         cp_async_commit();
       }
     }
@@ -806,10 +812,14 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
     const int n_own = c.n_own;
     const size_t D = c.D;
     const float2* slot1 = (const float2*)p.basis;  // basis slot k at slot1 + (k - 1) D
-    for (int k = 0; k < meff; ++k) {
+    // The basis vectors are read newest first: the slice has just written all m of them (8 MB
+    // each at L=20) and L2 still holds the latest ones, while in order of age every read would
+    // evict the next vector needed before it is reached.
+    for (int i = 0; i < meff; ++i) {
       cp_async_wait<kRecombDepth - 1>();  // this thread's copies of basis vector k have landed
+      const int k = meff - 1 - i;
       const float a = ss.coef_re_f[k], b = ss.coef_im_f[k];
-      const float4* q = stg + (size_t)(k % kRecombDepth) * 8 * kThreads + tid;
+      const float4* q = stg + (size_t)(i % kRecombDepth) * 8 * kThreads + tid;
 #pragma unroll
       for (int ct = 0; ct < 2; ++ct) {
         if (ct < n_own) {
@@ -823,9 +833,11 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
           }
         }
       }
-      if (k + kRecombDepth < meff)
-        recomb_issue(slot1 + (size_t)(k + kRecombDepth - 1) * D, rb, n_own,
-                     stg + (size_t)(k % kRecombDepth) * 8 * kThreads);
+      if (i + kRecombDepth < meff) {
+        const int kn = meff - 1 - (i + kRecombDepth);
+        recomb_issue(kn == 0 ? (const float2*)src : slot1 + (size_t)(kn - 1) * D, rb, n_own,
+                     stg + (size_t)(i % kRecombDepth) * 8 * kThreads);
+      }
       cp_async_commit();
     }
     cp_async_wait<0>();
