@@ -200,3 +200,41 @@ def test_sector_taylor_gradient_improves_on_the_centred_one():
         _, g, _ = run(A.SectorSpec(L, K, 1), A.Options(N, dt, m, prec="c128", grad=grad), u[None, :], psi0, f)
         errs[grad] = nrel(g[0], g_ex)
     assert errs["taylor2"] < 0.2 * errs["centered"], errs
+
+
+def test_sector_pulse_time_limit_ends_with_a_status_and_the_context_survives():
+    # Failure detection without a fault: with a 1 us wait limit the per-pulse limit is 60 us, far
+    # below one pulse of pe_L10_K4; every CTA gives up at a slice boundary with KG_ERR_TIMEOUT.
+    # Afterwards the same engine evaluates normally.
+    from paper_2010_03598_gb300 import _abi
+    A = api()
+    c, u, psi0, f = problem(10, 4, 1, 440, seed=3, target="last")
+    dev = torch.device("cuda", 0)
+    eng = A.KGrapeSector(A.SectorSpec(10, 4, 1), A.Options(440, 0.5, 10, prec="c64"), B=2)
+    U = torch.tensor(np.stack([u, u]), device=dev)
+    p0, ft = torch.tensor(psi0, device=dev), torch.tensor(f, device=dev)
+    try:
+        A.set_wait_limit_ns(1000)
+        eng.evaluate(U, p0, ft)
+        with pytest.raises(_abi.KGrapeError) as err:
+            eng.sync()
+        assert err.value.status == _abi.KG_ERR_TIMEOUT
+        assert np.isnan(eng.fid.cpu().numpy()).all()
+    finally:
+        A.set_wait_limit_ns(500_000_000)
+    fid, _ = eng.evaluate(U, p0, ft)
+    eng.sync()
+    F_ref = oracle.evaluate(c, u, 0.5, 10, psi0, f, "none")[0]
+    assert abs(float(fid[0].item()) - F_ref) / F_ref <= TOL["c64"][0]
+    eng.close()
+
+
+def test_sector_non_finite_control_is_reported():
+    from paper_2010_03598_gb300 import _abi
+    A = api()
+    c, u, psi0, f = problem(8, 3, 1, 20, seed=4, target="last")
+    u = u.copy()
+    u[5] = np.nan
+    with pytest.raises(_abi.KGrapeError) as err:
+        run(A.SectorSpec(8, 3, 1), A.Options(20, 0.5, 10, prec="c64"), u[None, :], psi0, f)
+    assert err.value.status == _abi.KG_ERR_NONFINITE
