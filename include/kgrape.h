@@ -303,14 +303,14 @@ kg_status kg_sector_states(const kg_sector* sector, uint64_t* states, int32_t D)
 kg_status kg_sector_apply_h0(const kg_sector* sector, const double* v, double* w, int32_t D);
 
 /* Workspace bytes for B pulses with options opts (N, m <= 32, prec, grad NONE / CENTERED / ZEROTH /
- * TAYLOR1 / TAYLOR2,
+ * EXACT / TAYLOR1 / TAYLOR2 (EXACT keeps 2N interior states per CTA),
  * dt, breakdown_tol, ctas = most CTAs to use (0 = every one that fits); ckpt_every and tile_bits
  * must be 0; flags: KG_FLAG_PHASE_TIMING only, recording CTA 0's cycles in kg_report.phase_cycles as
  * [0] Lanczos gathers and updates, [1] block reductions, [4] tridiagonal T and small exponential,
  * [5] recombination, [6] pulse setup and overlaps, [7] total).  The workspace holds one trajectory psi_0..psi_N per CTA of the launch, so it
  * is sized for the grid kg_sector_create will choose on the current device (min(B, resident CTAs,
- * ctas); B CTAs if no device is visible).  KG_ERR_UNSUPPORTED for KG_GRAD_EXACT, checkpoints, or a
- * subspace too large for one CTA's shared memory. */
+ * ctas); B CTAs if no device is visible).  KG_ERR_UNSUPPORTED for checkpoints or a subspace too large
+ * for one CTA's shared memory. */
 kg_status kg_sector_workspace_bytes(const kg_sector* sector, const kg_options* opts, int32_t B, size_t* bytes);
 
 /* Create a handle for B pulses on the current device, a caller-owned 256-byte aligned workspace of

@@ -59,6 +59,7 @@ struct SectorParams {
   double* grad;                  // [B][N] or null
   void* traj;                    // [grid][N+1][D] psi_0..psi_N of the pulse in hand
   void* basis;                   // [grid][m][D] Lanczos vectors of the slice in hand
+  void* tint;                    // [grid][2N][D] interior Gauss-Lobatto states (KG_GRAD_EXACT), or null
   double* G;                     // [grid][N+1]
   double* scal;                  // [B][kScCount]
   int* ctrl;                     // status word
@@ -84,8 +85,8 @@ struct SecSmem {
   double alpha[kMaxM], beta[kMaxM + 1];
   float alpha_f[kMaxM], beta_f[kMaxM + 1];
   float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
-  float coef_f[2][kMaxM];
-  double coef_d[2][kMaxM];
+  float coef_f[3][2][kMaxM];   // [slice end, interior node a, b][re, im][k]
+  double coef_d[3][2][kMaxM];
   double beta_m, nrm_d, ex_d, tay_d, err_max;
   float beta_m_f, inv_f;
   unsigned ff_e_set;
@@ -289,6 +290,54 @@ __device__ __noinline__ typename VecTraits<V>::R sec_taylor(const SectorParams& 
   return pt;
 }
 
+// Interior Gauss-Lobatto states of a slice (KG_GRAD_EXACT), from the slice's basis and the
+// coefficients warps 1 and 2 formed: forward (lob = 1) psi(t_{j-1} + s) for s = s_a, s_b, stored
+// to io[0..D), io[D..2D); backward (lob = 2) chi(t_{j-1} + s), overlapped with those stored states:
+// the return value is this thread's share of Im <chi_a|Hc|psi_a> + Im <chi_b|Hc|psi_b>.  Out of line,
+// so that its arrays stay out of the Lanczos loop's registers.
+template <class V, int NT, int RPT>
+__device__ __noinline__ typename VecTraits<V>::R sec_interior(const SectorParams& p, SecSmem& sm, const V* basis,
+                                                            int meff, int lob, V* io) {
+  using R = typename VecTraits<V>::R;
+  constexpr bool F32 = sizeof(R) == 4;
+  const int tid = threadIdx.x, D = p.D;
+  const int npc = __popc(p.hc_mask);
+  R pg = 0;
+  for (int w = 1; w <= 2; ++w) {
+    V y[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) y[i] = vmake<V>(0, 0);
+    for (int k = 0; k < meff; ++k) {
+      const R a = F32 ? (R)sm.coef_f[w][0][k] : (R)sm.coef_d[w][0][k];
+      const R b = F32 ? (R)sm.coef_f[w][1][k] : (R)sm.coef_d[w][1][k];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int r = tid + NT * i;
+        if (r < D) {
+          const V q = basis[(size_t)k * D + r];
+          y[i].x = fma(a, q.x, fma(-b, q.y, y[i].x));
+          y[i].y = fma(a, q.y, fma(b, q.x, y[i].y));
+        }
+      }
+    }
+    V* slot = io + (size_t)(w - 1) * D;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int r = tid + NT * i;
+      if (r >= D) continue;
+      if (lob == 1) {
+        slot[r] = y[i];
+      } else {
+        const unsigned st = p.states[r];
+        const R hc = (R)(0.5 * p.hc_amp * (double)(npc - 2 * __popc(st & p.hc_mask)));
+        const V o = slot[r];
+        pg = fma(hc, y[i].x * o.y - y[i].y * o.x, pg);  // Im(conj(chi_s) Hc psi_s), Hc diagonal
+      }
+    }
+  }
+  return pg;
+}
+
 // One slice: x (own rows, norm nrm) -> x = ||x|| V exp(-i tau T) e_1 (App. A), written to dst
 // (if not null), then ||x||^2 and, for extra = 1, G = Im <x| Hc |other> over the own rows are
 // reduced.  Returns false after a non-finite coefficient (status set).
@@ -299,7 +348,8 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
                                           const typename VecTraits<V>::R (&hh)[RPT], double uj, double tau,
                                           V (&x)[RPT], double& nrm, typename VecTraits<V>::R& inv, int extra,
                                           const V* other, V* dst, double& ex, int taylor = 0,
-                                          const V* psi_end = nullptr, double* tay = nullptr) {
+                                          const V* psi_end = nullptr, double* tay = nullptr, int lob = 0,
+                                          V* tint_io = nullptr) {
   using R = typename VecTraits<V>::R;
   constexpr bool F32 = sizeof(R) == 4;
   const int tid = threadIdx.x, D = p.D, m = p.m, ne = p.ell;
@@ -453,7 +503,8 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
     sec_sync();
   }
   sec_mark(p, sm, 0);
-  // ---- T (FP64), exp(-i tau T) e_1 and the recombination coefficients (warp 0)
+  // ---- T (FP64), exp(-i tau T) e_1 and the recombination coefficients (warp 0; with lob, warps 1
+  // and 2 form the coefficients of the two interior Gauss-Lobatto nodes at the same time)
   if (tid < 32) {
     __syncwarp();  // thread 0's stores of the step sums are visible to the warp
     const int k = tid;
@@ -473,15 +524,26 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
       }
       __syncwarp();
     }
+  }
+  if (lob) sec_sync();  // T is read by warps 1 and 2 as well
+  if (tid < (lob ? 96 : 32)) {
+    const int w = tid >> 5, k = tid & 31;
+    // slice end, or the interior nodes s_a, s_b = (1 -+ 1/sqrt 5) dt/2: forward exp(-i s H) psi_{j-1},
+    // backward exp(+i (dt - s) H) chi_j
+    double tw = tau;
+    if (w > 0) {
+      const double sn = 0.5 * p.dt * (1.0 + (w == 1 ? -1.0 : 1.0) / sqrt(5.0));
+      tw = (lob == 1) ? sn : -(p.dt - sn);
+    }
     double cr = 0.0, ci = 0.0;
     float tnorm = 0.f;
     const double etol = F32 ? 1e-13 : 1e-18;
-    // The exponential takes ceil(||tau T||) sub-steps: refuse a T whose Gershgorin bound is not a
+    // The exponential takes ceil(||tau T|| / 4) sub-steps: refuse a T whose Gershgorin bound is not a
     // finite, sane number (it would come from corrupted coefficients) instead of looping on it.
     float row = 0.f;
     if (k < meff)
-      row = fabsf((float)tau) * (fabsf(sm.alpha_f[k]) + (k >= 1 ? sm.beta_f[k] : 0.f) +
-                                 (k + 1 < meff ? sm.beta_f[k + 1] : 0.f));
+      row = fabsf((float)tw) * (fabsf(sm.alpha_f[k]) + (k >= 1 ? sm.beta_f[k] : 0.f) +
+                                (k + 1 < meff ? sm.beta_f[k + 1] : 0.f));
     row = (row == row) ? row : 3.0e38f;  // NaN -> refused
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) row = fmaxf(row, __shfl_xor_sync(0xffffffffu, row, o));
@@ -492,14 +554,14 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
       sm.abort = 1;
     }
     if (meff > 0 && sane)
-      tridiag_expv_e1(sm.alpha, sm.beta, sm.alpha_f, sm.beta_f, meff, tau, (float)tau, etol, cr, ci, tnorm);
+      tridiag_expv_e1(sm.alpha, sm.beta, sm.alpha_f, sm.beta_f, meff, tw, (float)tw, etol, cr, ci, tnorm);
     if (k < meff) {
-      sm.coef_d[0][k] = cr * nrm;
-      sm.coef_d[1][k] = ci * nrm;
-      sm.coef_f[0][k] = (float)(cr * nrm);
-      sm.coef_f[1][k] = (float)(ci * nrm);
+      sm.coef_d[w][0][k] = cr * nrm;
+      sm.coef_d[w][1][k] = ci * nrm;
+      sm.coef_f[w][0][k] = (float)(cr * nrm);
+      sm.coef_f[w][1][k] = (float)(ci * nrm);
     }
-    if (k == meff - 1) {  // a-posteriori indicator ||x|| b_m |c_{m-1}| (0 after a breakdown)
+    if (w == 0 && k == meff - 1) {  // a-posteriori indicator ||x|| b_m |c_{m-1}| (0 after a breakdown)
       double cm = nrm * sqrt(cr * cr + ci * ci);
       if (cm == 0.0 && !broke) {
         cm = nrm;
@@ -541,8 +603,8 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
 #pragma unroll
     for (int u = 0; u < KB; ++u) {
       const int k = k0 + u;
-      const R a = (k < meff) ? (F32 ? (R)sm.coef_f[0][k] : (R)sm.coef_d[0][k]) : (R)0;
-      const R b = (k < meff) ? (F32 ? (R)sm.coef_f[1][k] : (R)sm.coef_d[1][k]) : (R)0;
+      const R a = (k < meff) ? (F32 ? (R)sm.coef_f[0][0][k] : (R)sm.coef_d[0][0][k]) : (R)0;
+      const R b = (k < meff) ? (F32 ? (R)sm.coef_f[0][1][k] : (R)sm.coef_d[0][1][k]) : (R)0;
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
         y[i].x = fma(a, q[u][i].x, fma(-b, q[u][i].y, y[i].x));
@@ -567,6 +629,7 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
   // ---- Taylor hierarchy (App. B, Eq. gradp), backward slice j (sec_taylor)
   R pt = 0;
   if (taylor > 0) pt = sec_taylor<V, NT, RPT>(p, sm, Sa, Sb, ell, basis, uj, meff, nin, taylor, psi_end);
+  if (lob > 0) pt = sec_interior<V, NT, RPT>(p, sm, basis, meff, lob, tint_io);
   if constexpr (F32) {
     const float vals[3] = {pn, pg, pt};
     FF o[3];
@@ -586,7 +649,7 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
       sm.nrm_d = n;
       sm.inv_f = (n > 0.0) ? (float)(1.0 / n) : 0.f;
       sm.ex_d = (extra == 1) ? ff_to_double(o[1]) : 0.0;
-      sm.tay_d = (taylor > 0) ? ff_to_double(o[2]) : 0.0;
+      sm.tay_d = (taylor > 0 || lob == 2) ? ff_to_double(o[2]) : 0.0;
     }
     sec_sync();
     nrm = sm.nrm_d;
@@ -687,9 +750,12 @@ __device__ __forceinline__ void sec_eval(const SectorParams& p, int b, SecSmem& 
   R inv = (nrm > 0.0) ? (R)(1.0 / nrm) : (R)0;
   double ex = 0.0;
   sec_mark(p, sm, 6);
+  const bool exact = (p.grad_mode == KG_GRAD_EXACT);
+  V* tint = exact ? (V*)p.tint + (size_t)blockIdx.x * 2 * (size_t)N * D : nullptr;
   for (int j = 1; j <= N; ++j) {
     if (!sec_slice<V, NT, RPT>(p, sm, par, S0, S1, ell, basis, dd, hh, u[j - 1], p.dt, x, nrm, inv, 0, nullptr,
-                               traj + (size_t)j * D, ex)) {
+                               traj + (size_t)j * D, ex, 0, nullptr, nullptr, exact ? 1 : 0,
+                               exact ? tint + (size_t)2 * (j - 1) * D : nullptr)) {
       if (tid == 0) sec_abandon(p, sm, b, j);
       return;
     }
@@ -740,18 +806,21 @@ __device__ __forceinline__ void sec_eval(const SectorParams& p, int b, SecSmem& 
       // chi_{j-1} = exp(+i dt H_j) chi_j, fused G_{j-1} = 2 dt Im <chi_{j-1}|Hc|psi_{j-1}>
       double tay = 0.0;
       if (!sec_slice<V, NT, RPT>(p, sm, par, S0, S1, ell, basis, dd, hh, u[j - 1], -p.dt, x, nrm, inv, 1,
-                                 traj + (size_t)(j - 1) * D, nullptr, ex, taylor, traj + (size_t)j * D, &tay)) {
+                                 traj + (size_t)(j - 1) * D, nullptr, ex, taylor, traj + (size_t)j * D, &tay,
+                                 exact ? 2 : 0, exact ? tint + (size_t)2 * (j - 1) * D : nullptr)) {
         if (tid == 0) sec_abandon(p, sm, b, -j);
         return;
       }
       if (tid == 0) {
         G[j - 1] = 2.0 * p.dt * ex;
         if (taylor) G[j] = 2.0 * p.dt * tay;  // slice j's Taylor-hierarchy value replaces G_j
+        if (exact)  // 4-point Gauss-Lobatto over slice j: weights 1/12, 5/12, 5/12, 1/12
+          p.grad[(size_t)b * N + (j - 1)] = (G[j - 1] + G[j]) / 12.0 + (5.0 / 12.0) * 2.0 * p.dt * tay;
       }
     }
     sec_sync();  // G complete (written by thread 0)
     double* gb = p.grad + (size_t)b * N;
-    for (int j = tid; j < N; j += NT)
+    for (int j = tid; j < N && !exact; j += NT)
       gb[j] = (p.grad_mode == KG_GRAD_CENTERED) ? 0.5 * (G[j] + G[j + 1]) : G[j + 1];  // zeroth, Taylor
   }
   if (tid == 0) {
@@ -961,7 +1030,7 @@ bool build_basis(const kg_sector* s, size_t limit, bool want_ell, SectorBasis& o
 }
 
 struct SectorLayout {
-  size_t ctrl = 0, scal = 0, prof = 0, G = 0, basis = 0, traj = 0, ell = 0, states = 0, total = 0;
+  size_t ctrl = 0, scal = 0, prof = 0, G = 0, basis = 0, traj = 0, tint = 0, ell = 0, states = 0, total = 0;
 };
 
 size_t align_up(size_t x) { return (x + kg::kAlign - 1) / kg::kAlign * kg::kAlign; }
@@ -981,6 +1050,7 @@ SectorLayout sector_layout(int D, int ell, const kg_options* o, int B, int grid)
   l.G = take(sizeof(double) * (size_t)(o->N + 1) * grid);
   l.basis = take(vb * (size_t)o->m * grid);
   l.traj = take(vb * (size_t)(o->N + 1) * grid);
+  l.tint = take(o->grad == KG_GRAD_EXACT ? vb * 2 * (size_t)o->N * grid : 0);
   l.ell = take((size_t)ell * D * 2);
   l.states = take(sizeof(unsigned) * (size_t)D);
   l.total = off;
@@ -994,10 +1064,9 @@ kg_status check_sector_opts(const kg_options* o, int B) {
   if (o->m < 1 || o->m > kg::kMaxM) return host_fail(KG_ERR_INVALID_ARG, "m must satisfy 1 <= m <= 32");
   if (o->prec != KG_PREC_C128 && o->prec != KG_PREC_C64_F64REC)
     return host_fail(KG_ERR_INVALID_ARG, "prec must be KG_PREC_C128 or KG_PREC_C64_F64REC");
-  if (o->grad == KG_GRAD_EXACT) return host_fail(KG_ERR_UNSUPPORTED, "KG_GRAD_EXACT is not available for subspaces");
   if (o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED && o->grad != KG_GRAD_ZEROTH &&
-      o->grad != KG_GRAD_TAYLOR1 && o->grad != KG_GRAD_TAYLOR2)
-    return host_fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, _CENTERED, _ZEROTH, _TAYLOR1 or _TAYLOR2");
+      o->grad != KG_GRAD_EXACT && o->grad != KG_GRAD_TAYLOR1 && o->grad != KG_GRAD_TAYLOR2)
+    return host_fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, _CENTERED, _ZEROTH, _EXACT, _TAYLOR1 or _TAYLOR2");
   if (o->ckpt_every != 0) return host_fail(KG_ERR_UNSUPPORTED, "subspace evaluations keep every state: ckpt_every must be 0");
   if (o->tile_bits != 0) return host_fail(KG_ERR_INVALID_ARG, "tile_bits must be 0 for subspaces");
   if ((o->flags & ~KG_FLAG_PHASE_TIMING) != 0)
@@ -1225,6 +1294,7 @@ kg_status kg_sector_evaluate(kg_sector_handle* h, const double* u, const void* p
   p.grad = grad;
   p.traj = ws + h->lay.traj;
   p.basis = ws + h->lay.basis;
+  p.tint = (o.grad == KG_GRAD_EXACT) ? (void*)(ws + h->lay.tint) : nullptr;
   p.G = (double*)(ws + h->lay.G);
   p.scal = (double*)(ws + h->lay.scal);
   p.ctrl = (int*)(ws + h->lay.ctrl);

@@ -55,7 +55,7 @@ def test_asymmetric_mask_is_fine_without_parity():
 
 
 @pytest.mark.parametrize("opts_kw,status", [
-    (dict(grad="exact"), _abi.KG_ERR_UNSUPPORTED),
+    (dict(grad="exact"), _abi.KG_OK),
     (dict(grad="taylor1"), _abi.KG_OK),
     (dict(grad="taylor2"), _abi.KG_OK),
     (dict(ckpt_every=4), _abi.KG_ERR_UNSUPPORTED),
@@ -101,3 +101,10 @@ def test_full_chain_refuses_taylor_gradients(grad):
     n = ctypes.c_size_t(0)
     assert _abi.lib().kg_workspace_bytes(ctypes.byref(ch.to_c()), ctypes.byref(o.to_c()),
                                          ctypes.byref(n)) == _abi.KG_ERR_UNSUPPORTED
+
+
+def test_exact_gradient_workspace_keeps_the_interior_states():
+    spec = A.SectorSpec(10, 4, 1)
+    c = A.Options(N=440, dt=0.5, m=10, prec="c64")
+    e = A.Options(N=440, dt=0.5, m=10, prec="c64", grad="exact")
+    assert A.sector_workspace_bytes(spec, e, 1) - A.sector_workspace_bytes(spec, c, 1) >= 2 * 440 * 110 * 8

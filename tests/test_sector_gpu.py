@@ -238,3 +238,37 @@ def test_sector_non_finite_control_is_reported():
     with pytest.raises(_abi.KGrapeError) as err:
         run(A.SectorSpec(8, 3, 1), A.Options(20, 0.5, 10, prec="c64"), u[None, :], psi0, f)
     assert err.value.status == _abi.KG_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("L,K,parity,N,prec", [
+    (10, 4, 1, 120, "c128"),
+    (10, 4, 1, 120, "c64"),
+    (8, 3, -1, 40, "c64"),     # 128 x 4
+    (17, 4, 1, 16, "c64"),     # 256 x 8
+    (20, 4, 1, 10, "c64"),     # 256 x 10
+    (20, 4, 1, 6, "c128"),     # 512 x 8
+    (3, 1, 1, 20, "c128"),     # D = 2 < m
+])
+def test_sector_exact_gradient_vs_oracle(L, K, parity, N, prec):
+    # App. B, Eqs. natu_integr / natgrad with the 4-point Gauss-Lobatto rule: the interior states come
+    # from the slice's own basis with the coefficients of the interior node lengths
+    A = api()
+    c, u, psi0, f = problem(L, K, parity, N, seed=L * 11 + K, target="random")
+    m, dt = 10, 0.5
+    F_ref, g_ref, _ = oracle.evaluate(c, u, dt, m, psi0, f, "exact")
+    fid, g, _ = run(A.SectorSpec(L, K, parity), A.Options(N, dt, m, prec=prec, grad="exact"), u[None, :], psi0, f)
+    tf, tg = TOL[prec]
+    assert abs(fid[0] - F_ref) / F_ref <= tf
+    assert nrel(g[0], g_ref) <= tg, nrel(g[0], g_ref)
+
+
+def test_sector_exact_gradient_matches_the_dense_derivative():
+    A = api()
+    L, K, N, dt, m = 8, 3, 16, 0.05, 12
+    c, u, psi0, f = problem(L, K, 1, N, seed=5, target="random")
+    _, g_ex = oracle.exact_gradient(c, u, dt, psi0, f)
+    errs = {}
+    for grad in ("centered", "exact"):
+        _, g, _ = run(A.SectorSpec(L, K, 1), A.Options(N, dt, m, prec="c128", grad=grad), u[None, :], psi0, f)
+        errs[grad] = nrel(g[0], g_ex)
+    assert errs["exact"] < 1e-3 * errs["centered"], errs
