@@ -87,7 +87,7 @@ struct SecSmem {
   float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
   float coef_f[3][2][kMaxM];   // [slice end, interior node a, b][re, im][k]
   double coef_d[3][2][kMaxM];
-  double beta_m, nrm_d, ex_d, tay_d, err_max;
+  double nrm_d, ex_d, tay_d, err_max;
   float beta_m_f, inv_f;
   unsigned ff_e_set;
   int breakdowns;
@@ -469,10 +469,7 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
     beta = sqrt(fmax(b2, (R)0));
     if (tid == 0) {
       sm.alpha_f[k] = (float)alpha;
-      if (last) {
-        sm.beta_m_f = (float)beta;
-        if (!F32) sm.beta_m = (double)beta;
-      }
+      if (last) sm.beta_m_f = (float)beta;  // b_m of the error indicator
     }
     if (last) break;
     amax = fmax(amax, fabs(alpha));
@@ -649,7 +646,7 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
       sm.nrm_d = n;
       sm.inv_f = (n > 0.0) ? (float)(1.0 / n) : 0.f;
       sm.ex_d = (extra == 1) ? ff_to_double(o[1]) : 0.0;
-      sm.tay_d = (taylor > 0 || lob == 2) ? ff_to_double(o[2]) : 0.0;
+      sm.tay_d = (taylor > 0 || lob == 2) ? ff_to_double(o[2]) : 0.0;  // Taylor or interior overlaps
     }
     sec_sync();
     nrm = sm.nrm_d;
