@@ -108,3 +108,33 @@ def test_exact_gradient_workspace_keeps_the_interior_states():
     c = A.Options(N=440, dt=0.5, m=10, prec="c64")
     e = A.Options(N=440, dt=0.5, m=10, prec="c64", grad="exact")
     assert A.sector_workspace_bytes(spec, e, 1) - A.sector_workspace_bytes(spec, c, 1) >= 2 * 440 * 110 * 8
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 5, 6, 7, 8, 9])
+def test_every_small_subspace_matches_the_oracle(L):
+    # every excitation number and parity of the short chains: the basis bit for bit, the kernel's
+    # H0 tables against Q H_K Q^T (with an asymmetric-in-Jz coupling so that no term hides)
+    rng = np.random.default_rng(L)
+    for K in range(L + 1):
+        for parity in (1, -1, 0):
+            states = S.k_sector_states(L, K)
+            reps = S.pe_change_of_basis(states, L, parity)[1]
+            if reps.shape[0] == 0:
+                continue  # e.g. the odd subspace of a sector of palindromes only
+            spec = A.SectorSpec(L, K, parity, Jxy=0.9, Jz=1.7)
+            assert A.sector_dim(spec) == reps.shape[0]
+            np.testing.assert_array_equal(A.sector_states(spec).astype(np.int64), reps)
+            c = S.SectorChain(L, K, parity, 0.9, 1.7, 1 | (1 << (L - 1)), 1.0)
+            v = rng.standard_normal(c.D) + 1j * rng.standard_normal(c.D)
+            np.testing.assert_allclose(A.sector_apply_h0(spec, v), c.apply_H0(v), rtol=0, atol=1e-13 * np.abs(v).sum())
+
+
+def test_empty_subspace_is_reported_and_refused():
+    # K = 0 on two sites: the only state |00> is a palindrome, so the odd subspace is empty
+    spec = A.SectorSpec(2, 0, -1)
+    assert A.sector_dim(spec) == 0
+    o = A.Options(N=4, dt=0.5, m=4)
+    h = ctypes.c_void_p(0)
+    st = _abi.lib().kg_sector_create(ctypes.byref(h), ctypes.byref(spec.to_c()), ctypes.byref(o.to_c()), 1,
+                                     ctypes.c_void_p(256), ctypes.c_size_t(1 << 20), None)
+    assert st == _abi.KG_ERR_INVALID_ARG
