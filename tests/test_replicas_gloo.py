@@ -64,3 +64,21 @@ def test_reference_arm_prints_on_rank_zero_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], capture_output=True, text=True, env=env, timeout=300, cwd=ROOT)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_algorithmic_bytes_of_the_benchmark_lines():
+    # D-vector passes of the basis-storing Lanczos, P = N (2 (4m - 1) + 1) + 2 (+ N (4m - 1) with
+    # checkpoint recompute): 533.5 GB for L=20, N=400, m=20 in complex64, twice that in complex128,
+    # 15.35 TB for L=24, N=400, m=24 with checkpoints every 20
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2010_03598_gb300 import workloads as W
+
+    w20 = W.WORKLOADS["xxz_L20_N400_m20"]
+    assert bench.alg_bytes(w20, "c64") == (400 * 159 + 2) * (1 << 20) * 8
+    assert abs(bench.alg_bytes(w20, "c64") / 1e9 - 533.5) < 0.1
+    assert bench.alg_bytes(w20, "c128") == 2 * bench.alg_bytes(w20, "c64")
+    w24 = W.WORKLOADS["xxz_L24_N400_m24_ckpt20"]
+    assert abs(bench.alg_bytes(w24, "c64", w24.ckpt) / 1e12 - 15.35) < 0.01
+    # the exact gradient adds two recombinations per slice and direction and the stored interior states
+    assert bench.alg_bytes(w20, "c64", 0, "exact") - bench.alg_bytes(w20, "c64") == 400 * (4 * 21 + 2) * (1 << 20) * 8
