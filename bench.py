@@ -45,10 +45,12 @@ def parse_args():
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--N", type=int, default=0, help="shorter pulse (profiling a small case); 0 = workload's N")
-    ap.add_argument("--grad", choices=["centered", "zeroth", "exact"], default="centered",
-                    help="gradient mode of the timed evaluations (the headline is the centred gradient)")
+    ap.add_argument("--grad", choices=["centered", "zeroth", "exact", "taylor1", "taylor2"], default="centered",
+                    help="gradient mode of the timed evaluations (the headline is the centred gradient; "
+                         "taylor1/2 on subspace workloads only)")
     ap.add_argument("--reorth", action="store_true", help="full re-orthogonalisation of every Lanczos step")
-    ap.add_argument("--batch", type=int, default=0, help="pulses of a subspace workload (0: two per SM)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="pulses of a subspace workload (0: one per resident CTA of the subspace kernel)")
     return ap.parse_args()
 
 
@@ -495,6 +497,22 @@ print(json.dumps(dict(seconds=time.perf_counter() - t0, slices={slices})))
 """
 
 
+def resident_pulses(A, spec, w, D, prec, dev) -> int:
+    """Pulses that fill every CTA the subspace kernel keeps resident (one pulse per CTA): the grid a
+    probe engine (two slices, more pulses than fit) chooses on this device."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    probe = A.KGrapeSector(spec, A.Options(2, w.dt, w.m, prec=prec, grad="none"), B=8 * sms)
+    z = torch.zeros(8 * sms, 2, dtype=torch.float64, device=dev)
+    e = torch.zeros(D, dtype=torch.complex128, device=dev)
+    e[0] = 1.0
+    probe.evaluate(z, e, e)
+    ctas = int(probe.sync()["ctas"])
+    probe.close()
+    return ctas
+
+
 def run_sector(args):
     """Sec. 3.1-3.2's own setting: B pulses of the e_1 -> e_D task in one PE subspace, one CTA per pulse."""
     import torch
@@ -508,12 +526,11 @@ def run_sector(args):
     w = W.SECTOR_WORKLOADS[args.workload]
     spec = A.SectorSpec(w.L, w.K, w.parity, Jxy=2.0 * w.J, Jz=2.0 * w.J * w.alpha_z, hc_amp=w.J)
     D = A.sector_dim(spec)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    B = args.batch if args.batch > 0 else 2 * sms
+    B = args.batch if args.batch > 0 else resident_pulses(A, spec, w, D, args.prec, dev)
     U, psi0, f = W.sector_instance(w, D, batch=B)
     N = U.shape[1]
     ut, pt, ft = torch.tensor(U, device=dev), torch.tensor(psi0, device=dev), torch.tensor(f, device=dev)
-    eng = A.KGrapeSector(spec, A.Options(N, w.dt, w.m, prec=args.prec), B=B)
+    eng = A.KGrapeSector(spec, A.Options(N, w.dt, w.m, prec=args.prec, grad=args.grad), B=B)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         eng.evaluate(ut, pt, ft)
@@ -535,7 +552,8 @@ def run_sector(args):
     rep = eng.sync()
     ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     value = B * args.steps / (sum(ms) / 1e3)
-    # algorithmic bytes as for the full chain (D-vector passes of the basis-storing Lanczos), per pulse
+    # algorithmic bytes as for the full chain (D-vector passes of the basis-storing Lanczos with the
+    # centred gradient), per pulse; the other gradient modes are timed against the same count
     s = 8 if args.prec == "c64" else 16
     ab = B * (N * (2 * (4 * w.m - 1) + 1) + 2) * D * s
     hbm, kind = measured_peaks()
@@ -579,6 +597,7 @@ def run_sector(args):
            "vs_baseline": None, "dtype": "c64+f64" if args.prec == "c64" else "c128", "data": "synthetic",
            "config": {"workload": args.workload, "L": w.L, "K": w.K, "parity": w.parity, "D": D, "N": N, "m": w.m,
                       "dt": w.dt, "pulses": B, "task": "e_1 -> e_D", "J": w.J, "alpha_z": w.alpha_z,
+                      "grad": args.grad,
                       "hc": "(J/2)(sigma^z_1 + sigma^z_L)", "u": "U(-1,1)",
                       "l2": "flushed between timed steps (512 MiB write); per-step working set > L2",
                       "launch": "one CTA per pulse, state in shared memory"},
