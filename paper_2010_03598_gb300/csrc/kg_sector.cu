@@ -961,6 +961,24 @@ struct OrbitInfo {
 
 bool build_basis(const kg_sector* s, size_t limit, bool want_ell, SectorBasis& out, std::string& why) {
   const int L = s->L, K = s->K, P = s->parity;
+  // the dimension in closed form, to refuse large subspaces before enumerating them: C(L,K) states,
+  // pal of them mirror-symmetric (fixed by the first floor(L/2) bits and, for odd L, the middle one);
+  // D = C (parity 0), (C + pal)/2 (even), (C - pal)/2 (odd)
+  {
+    auto binom = [](int n, int k) {
+      double c = 1.0;
+      for (int i = 0; i < k; ++i) c = c * (double)(n - i) / (double)(i + 1);
+      return c;
+    };
+    const int h = L / 2;
+    const double C = binom(L, K);
+    const double pal = (L % 2 == 0) ? ((K % 2 == 0) ? binom(h, K / 2) : 0.0) : binom(h, K / 2);
+    const double Dd = (P == 0) ? C : 0.5 * (C + (double)P * pal);
+    if (Dd > (double)limit + 0.5) {
+      why = "subspace dimension " + std::to_string((long long)(Dd + 0.5)) + " exceeds " + std::to_string(limit);
+      return false;
+    }
+  }
   std::vector<uint64_t> all;  // the K-excitation states, ascending (Gosper's next-combination step)
   if (K == 0) {
     all.push_back(0);

@@ -138,3 +138,22 @@ def test_empty_subspace_is_reported_and_refused():
     st = _abi.lib().kg_sector_create(ctypes.byref(h), ctypes.byref(spec.to_c()), ctypes.byref(o.to_c()), 1,
                                      ctypes.c_void_p(256), ctypes.c_size_t(1 << 20), None)
     assert st == _abi.KG_ERR_INVALID_ARG
+
+
+def test_large_sectors_are_refused_without_enumerating_them():
+    import time
+    t0 = time.perf_counter()
+    D = ctypes.c_int32(0)
+    st = _abi.lib().kg_sector_dim(ctypes.byref(A.SectorSpec(30, 15, 1).to_c()), ctypes.byref(D))
+    assert st == _abi.KG_ERR_UNSUPPORTED and time.perf_counter() - t0 < 0.5
+    assert "dimension" in _abi.lib().kg_last_error().decode()
+
+
+def test_closed_form_limit_keeps_odd_subspaces_near_the_limit():
+    # L = 14, K = 7: C = 3432, no palindromes (odd K, even L): D = 1716 either parity -- accepted;
+    # L = 16, K = 8: C = 12870, 70 palindromes: even 6470, odd 6400 -- refused
+    assert A.sector_dim(A.SectorSpec(14, 7, -1)) == 1716
+    D = ctypes.c_int32(0)
+    for par in (1, -1):
+        assert _abi.lib().kg_sector_dim(ctypes.byref(A.SectorSpec(16, 8, par).to_c()),
+                                        ctypes.byref(D)) == _abi.KG_ERR_UNSUPPORTED
