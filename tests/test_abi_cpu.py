@@ -158,3 +158,46 @@ def test_package_import_does_not_need_the_library():
     import paper_2010_03598_gb300.workloads as w
     importlib.reload(w)
     assert w.neel_index(4) == 10
+
+
+def test_header_is_plain_c_and_a_c_program_links_against_the_library(lib, tmp_path):
+    # The boundary is a C ABI: the header compiles as C99, and a C caller links against
+    # libkgrape.so and calls the host-only entry points (no GPU needed for these).
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_2010_03598_gb300 import _abi
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "caller.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "kgrape.h"
+int main(void) {
+  kg_sector s = {20, 4, 1, 0, (1ull << 0) | (1ull << 19), 2.0, 1.0, 1.0};
+  int32_t D = 0;
+  if (kg_sector_dim(&s, &D) != KG_OK) { printf("error %s\n", kg_last_error()); return 1; }
+  kg_chain c = {8, KG_HC_SX_SITE, 0, 0, 0, 1.0, 0.5, 1.0};
+  kg_options o = {64, 12, KG_PREC_C64_F64REC, KG_GRAD_CENTERED, 0, 0, 0, 0, 0.1, 0.0};
+  size_t bytes = 0;
+  if (kg_workspace_bytes(&c, &o, &bytes) != KG_OK) { printf("error %s\n", kg_last_error()); return 1; }
+  o.m = 99;
+  int bad = kg_workspace_bytes(&c, &o, &bytes);
+  printf("%d %d %zu %d\n", kg_version(), D, bytes, bad);
+  return 0;
+}
+""")
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(_abi.LIB_PATH)
+    cmd = [gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"), str(src), "-o", str(exe),
+           "-L", libdir, "-l:libkgrape.so", f"-Wl,-rpath,{libdir}"]
+    cuda_lib = "/usr/local/cuda/lib64"
+    if os.path.isdir(cuda_lib):
+        cmd += [f"-Wl,-rpath,{cuda_lib}", f"-L{cuda_lib}"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    version, D, nbytes, bad = out.stdout.split()
+    assert int(D) == 2445 and int(nbytes) > 0 and int(bad) == _abi.KG_ERR_INVALID_ARG

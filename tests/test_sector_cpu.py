@@ -9,6 +9,16 @@ import oracle.sector as S
 from paper_2010_03598_gb300 import _abi
 from paper_2010_03598_gb300 import api as A
 
+@pytest.fixture(autouse=True, scope="module")
+def library():
+    # the host entry points live in libkgrape.so: build it in-tree if this checkout has none yet
+    import os
+    from paper_2010_03598_gb300 import build as kbuild
+    if not os.path.exists(_abi.LIB_PATH):
+        kbuild.build()
+    return _abi.lib()
+
+
 CASES = [(10, 4, 1), (14, 4, 1), (20, 4, 1), (8, 3, -1), (9, 4, 0), (5, 2, 1), (3, 1, 1), (12, 6, 1), (12, 6, -1),
          (2, 1, 1), (2, 1, -1), (6, 0, 1), (7, 7, 1), (17, 4, 1)]
 
