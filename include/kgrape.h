@@ -249,12 +249,16 @@ kg_status kg_batch_destroy(kg_batch* batch);
  * KG_FLAG_HOST_STAGING is not accepted.  Requests whose workspace (kg_workspace_bytes) exceeds
  * the array are rejected with KG_ERR_WORKSPACE before any device work.
  * The call is synchronous: it enqueues on cuda_stream (NULL = legacy default stream), waits
- * for it and returns the device status like kg_sync.  Every call on a device shares the one
- * array, which keeps the last call's contents (the control block is cleared at each call):
- * calls that overlap on the GPU — from several host threads or streams — race and give wrong
- * results.  The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress, which may load the library's device code); make that first call
- * outside any stream capture.  No device or host memory is allocated on the success path. */
+ * for it and returns the device status like kg_sync.  It must never be called while
+ * cuda_stream is being captured into a CUDA graph (the wait and the status read are illegal
+ * there): such calls are rejected with KG_ERR_INVALID_ARG before any device work.  Every call
+ * on a device shares the one array, which keeps the last call's contents (the control block is
+ * cleared at each call): calls that overlap on the GPU — from several host threads or streams —
+ * race and give wrong results.  The first call on a device, and the first after the device's
+ * context changed (cudaDeviceReset, or another context made current), resolves the array's
+ * device address in that context (cudaGetSymbolAddress, which may load the library's device
+ * code).  Without a current CUDA context the call returns KG_ERR_CUDA and launches nothing.
+ * No device or host memory is allocated on the success path. */
 kg_status kg_evaluate_static(const kg_chain* chain, const kg_options* opts, const double* u, const void* psi0,
                              const void* target, double* fid, double* grad, void* cuda_stream);
 

@@ -147,6 +147,56 @@ struct kg_handle {
   int launches = 0;
 };
 
+namespace {
+
+// Launch configuration of one evaluation on device dev (shared by kg_create and
+// kg_evaluate_static): tile size, kernel variant, CTA count, default breakdown tolerance.
+kg_status configure_handle(const kg_chain* chain, const kg_options* opts, const Layout& lay, int dev, kg_handle* h) {
+  const int t = default_tile_bits(chain, opts);
+  const int ntiles = 1 << (chain->L - t);
+  cudaError_t e;
+  // Resident variant when every CTA can keep its tiles in registers/shared memory.
+  int variant = kg::kVariantStreaming;
+  int ctas = 0;
+  const int tpc = kg::resident_tiles_per_cta(opts->prec);
+  if (tpc > 0 && !(opts->flags & KG_FLAG_FULL_REORTH)) {
+    int maxr = 0;
+    e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantResident, t, &maxr);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    // default: two tiles per CTA (paired so that every CTA has the same cross-tile work)
+    int c = (opts->ctas > 0) ? opts->ctas : (ntiles >= 2 ? ntiles / 2 : 1);
+    if (c > ntiles) c = ntiles;
+    if (c > maxr) c = maxr;
+    if (c > kg::kMaxCtas) c = kg::kMaxCtas;
+    if (c >= 1 && (long long)c * tpc >= ntiles) {
+      variant = (t == kg::max_tile_bits(opts->prec)) ? kg::kVariantResidentFull : kg::kVariantResident;
+      ctas = c;
+    }
+  }
+  if (variant == kg::kVariantStreaming && (opts->flags & KG_FLAG_FULL_REORTH)) variant = kg::kVariantGenericStream;
+  if (variant == kg::kVariantStreaming || variant == kg::kVariantGenericStream) {
+    int maxc = 0;
+    e = kg::eval_kernel_max_ctas(opts->prec, variant, t, &maxc);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (maxc < 1) return fail(KG_ERR_UNSUPPORTED, "evaluation kernel does not fit on this device");
+    ctas = (opts->ctas > 0) ? opts->ctas : ntiles;
+    if (ctas > ntiles) ctas = ntiles;
+    if (ctas > maxc) ctas = maxc;
+    if (ctas > kg::kMaxCtas) ctas = kg::kMaxCtas;
+  }
+  h->chain = *chain;
+  h->opts = *opts;
+  if (!(h->opts.breakdown_tol > 0.0)) h->opts.breakdown_tol = (opts->prec == KG_PREC_C128) ? 1e-12 : 1e-5;
+  h->lay = lay;
+  h->device = dev;
+  h->ctas = ctas;
+  h->t_bits = t;
+  h->variant = variant;
+  return KG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int kg_version(void) { return 100; }
@@ -188,49 +238,15 @@ kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options*
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  const int t = default_tile_bits(chain, opts);
-  const int ntiles = 1 << (chain->L - t);
-  // Resident variant when every CTA can keep its tiles in registers/shared memory.
-  int variant = kg::kVariantStreaming;
-  int ctas = 0;
-  const int tpc = kg::resident_tiles_per_cta(opts->prec);
-  if (tpc > 0 && !(opts->flags & KG_FLAG_FULL_REORTH)) {
-    int maxr = 0;
-    e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantResident, t, &maxr);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    // default: two tiles per CTA (paired so that every CTA has the same cross-tile work)
-    int c = (opts->ctas > 0) ? opts->ctas : (ntiles >= 2 ? ntiles / 2 : 1);
-    if (c > ntiles) c = ntiles;
-    if (c > maxr) c = maxr;
-    if (c > kg::kMaxCtas) c = kg::kMaxCtas;
-    if (c >= 1 && (long long)c * tpc >= ntiles) {
-      variant = (t == kg::max_tile_bits(opts->prec)) ? kg::kVariantResidentFull : kg::kVariantResident;
-      ctas = c;
-    }
-  }
-  if (variant == kg::kVariantStreaming && (opts->flags & KG_FLAG_FULL_REORTH)) variant = kg::kVariantGenericStream;
-  if (variant == kg::kVariantStreaming || variant == kg::kVariantGenericStream) {
-    int maxc = 0;
-    e = kg::eval_kernel_max_ctas(opts->prec, variant, t, &maxc);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    if (maxc < 1) return fail(KG_ERR_UNSUPPORTED, "evaluation kernel does not fit on this device");
-    ctas = (opts->ctas > 0) ? opts->ctas : ntiles;
-    if (ctas > ntiles) ctas = ntiles;
-    if (ctas > maxc) ctas = maxc;
-    if (ctas > kg::kMaxCtas) ctas = kg::kMaxCtas;
-  }
   kg_handle* h = new kg_handle();
-  h->chain = *chain;
-  h->opts = *opts;
-  if (!(h->opts.breakdown_tol > 0.0)) h->opts.breakdown_tol = (opts->prec == KG_PREC_C128) ? 1e-12 : 1e-5;
-  h->lay = lay;
+  st = configure_handle(chain, opts, lay, dev, h);
+  if (st != KG_OK) {
+    delete h;
+    return st;
+  }
   h->ws = (char*)workspace;
   h->bytes = bytes;
   h->stream = (cudaStream_t)cuda_stream;
-  h->device = dev;
-  h->ctas = ctas;
-  h->t_bits = t;
-  h->variant = variant;
   *handle = h;
   return KG_OK;
 }
@@ -378,19 +394,51 @@ static __device__ __align__(256) unsigned char g_static_ws[KG_STATIC_WORKSPACE_B
 namespace {
 
 constexpr int kStaticMaxDevices = 64;
-void* g_static_addr[kStaticMaxDevices];  // device address of g_static_ws, per device (set-up once)
-std::mutex g_static_mu;                  // guards the set-up only; calls themselves must not overlap
+// Device address of g_static_ws per device, and the context it was resolved in.  A symbol's
+// address belongs to one context: after cudaDeviceReset, or when the caller makes another
+// context current on the device, the address is resolved again.
+struct StaticAddr {
+  void* ctx = nullptr;
+  void* addr = nullptr;
+};
+StaticAddr g_static_addr[kStaticMaxDevices];
+std::mutex g_static_mu;  // guards the set-up only; calls themselves must not overlap
 
-// Set-up, once per device, with that device current.
+using CtxGetCurrentFn = int (*)(void**);  // the driver's cuCtxGetCurrent (CUresult, CUcontext*)
+
+// The current context of the calling thread (through the driver entry point the runtime hands
+// out, so that the library does not link the driver library itself).
+kg_status current_context(void** ctx) {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDriverEntryPointByVersion(cuCtxGetCurrent)");
+    if (q != cudaDriverEntryPointSuccess || !p) return fail(KG_ERR_CUDA, "cuCtxGetCurrent is not available");
+    fn = (CtxGetCurrentFn)p;
+  }
+  *ctx = nullptr;
+  if (fn(ctx) != 0 || !*ctx) return fail(KG_ERR_CUDA, "no current CUDA context on the calling thread");
+  return KG_OK;
+}
+
+// Set-up, once per device and context, with that device current: the device address of the
+// scratch array.
 kg_status static_scratch_address(int dev, void** out) {
+  void* ctx = nullptr;
+  kg_status st = current_context(&ctx);
+  if (st != KG_OK) return st;
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+  StaticAddr& a = g_static_addr[dev];
+  if (!a.addr || a.ctx != ctx) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-    g_static_addr[dev] = p;
+    a.ctx = ctx;
+    a.addr = p;
   }
-  *out = g_static_addr[dev];
+  *out = a.addr;
   return KG_OK;
 }
 
@@ -418,52 +466,21 @@ extern "C" kg_status kg_evaluate_static(const kg_chain* chain, const kg_options*
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kStaticMaxDevices) return fail(KG_ERR_UNSUPPORTED, "device index above 63");
+  // The call waits for its stream and reads the status back, which a stream capture forbids.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cap);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(KG_ERR_INVALID_ARG, "kg_evaluate_static is synchronous and cannot be called during stream capture");
   void* ws = nullptr;
   st = static_scratch_address(dev, &ws);
   if (st != KG_OK) return st;
-
-  // launch configuration: the same choice kg_create makes
-  const int t = default_tile_bits(chain, opts);
-  const int ntiles = 1 << (chain->L - t);
-  int variant = kg::kVariantStreaming;
-  int ctas = 0;
-  const int tpc = kg::resident_tiles_per_cta(opts->prec);
-  if (tpc > 0 && !(opts->flags & KG_FLAG_FULL_REORTH)) {
-    int maxr = 0;
-    e = kg::eval_kernel_max_ctas(opts->prec, kg::kVariantResident, t, &maxr);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    int c = (opts->ctas > 0) ? opts->ctas : (ntiles >= 2 ? ntiles / 2 : 1);
-    if (c > ntiles) c = ntiles;
-    if (c > maxr) c = maxr;
-    if (c > kg::kMaxCtas) c = kg::kMaxCtas;
-    if (c >= 1 && (long long)c * tpc >= ntiles) {
-      variant = (t == kg::max_tile_bits(opts->prec)) ? kg::kVariantResidentFull : kg::kVariantResident;
-      ctas = c;
-    }
-  }
-  if (variant == kg::kVariantStreaming && (opts->flags & KG_FLAG_FULL_REORTH)) variant = kg::kVariantGenericStream;
-  if (variant == kg::kVariantStreaming || variant == kg::kVariantGenericStream) {
-    int maxc = 0;
-    e = kg::eval_kernel_max_ctas(opts->prec, variant, t, &maxc);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    if (maxc < 1) return fail(KG_ERR_UNSUPPORTED, "evaluation kernel does not fit on this device");
-    ctas = (opts->ctas > 0) ? opts->ctas : ntiles;
-    if (ctas > ntiles) ctas = ntiles;
-    if (ctas > maxc) ctas = maxc;
-    if (ctas > kg::kMaxCtas) ctas = kg::kMaxCtas;
-  }
   kg_handle h;  // on the stack: nothing is allocated
-  h.chain = *chain;
-  h.opts = *opts;
-  if (!(h.opts.breakdown_tol > 0.0)) h.opts.breakdown_tol = (opts->prec == KG_PREC_C128) ? 1e-12 : 1e-5;
-  h.lay = lay;
+  st = configure_handle(chain, opts, lay, dev, &h);
+  if (st != KG_OK) return st;
   h.ws = (char*)ws;
   h.bytes = KG_STATIC_WORKSPACE_BYTES;
   h.stream = (cudaStream_t)cuda_stream;
-  h.device = dev;
-  h.ctas = ctas;
-  h.t_bits = t;
-  h.variant = variant;
   st = enqueue(&h, u, psi0, target, fid, grad);
   if (st != KG_OK) return st;
   return kg_sync(&h, nullptr);

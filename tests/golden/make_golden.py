@@ -25,6 +25,10 @@ CASES = [
     ("oracle_xxz_L8_N64_m12", "xxz_L8_N64_m12", None, ("centered", "zeroth")),
     ("oracle_xxz_L16_N200_m20", "xxz_L16_N200_m20", None, ("centered",)),
     ("oracle_xxz_L20_N2_m20", "xxz_L20_N400_m20", 2, ("centered", "zeroth")),
+    # the benchmarked pulse in full (about half an hour of one CPU core)
+    ("oracle_xxz_L20_N400_m20", "xxz_L20_N400_m20", None, ("centered",)),
+    # the checkpointed chain at its full size, on a 12-slice pulse (a few GB of host memory)
+    ("oracle_xxz_L24_N12_m24", "xxz_L24_N400_m24_ckpt20", 12, ("centered",)),
 ]
 
 

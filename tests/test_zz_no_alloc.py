@@ -36,6 +36,45 @@ def test_static_entry_point_rejects_a_workspace_above_its_limit():
     assert b"static scratch" in _abi.lib().kg_last_error()
 
 
+@pytest.mark.skipif(torch.cuda.is_available(), reason="needs a process without a CUDA device")
+def test_static_entry_point_without_a_context_returns_an_error_and_launches_nothing():
+    # No device, hence no context: the call must stop with a status before any launch.
+    from paper_2010_03598_gb300 import api as A
+    chain = A.ChainSpec(8)
+    opts = A.Options(4, 0.1, 6, prec="c64")
+    fake = 1 << 12  # aligned, never dereferenced: the call returns before any device work
+    st = _abi.lib().kg_evaluate_static(ctypes.byref(chain.to_c()), ctypes.byref(opts.to_c()), fake, fake, fake, fake,
+                                       fake, None)
+    assert st == _abi.KG_ERR_CUDA
+
+
+@pytest.mark.gpu
+def test_static_entry_point_refuses_a_capturing_stream():
+    # The call waits for its stream, which a capture forbids: it must refuse before any work and
+    # leave the capture intact.
+    from paper_2010_03598_gb300 import api as A
+    L, N, m = 8, 4, 6
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(7)
+    u = torch.tensor(rng.uniform(-1, 1, N), device=dev)
+    psi0 = torch.tensor(W.neel_state(L), device=dev)
+    f = torch.tensor(W.draw_target(rng, 1 << L), device=dev)
+    fid = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.zeros(N, dtype=torch.float64, device=dev)
+    chain, opts = A.ChainSpec(L), A.Options(N, 0.1, m, prec="c64")
+    s = torch.cuda.Stream(device=dev)
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        st = _abi.lib().kg_evaluate_static(ctypes.byref(chain.to_c()), ctypes.byref(opts.to_c()), u.data_ptr(),
+                                           psi0.data_ptr(), f.data_ptr(), fid.data_ptr(), grad.data_ptr(),
+                                           ctypes.c_void_p(s.cuda_stream))
+        g.capture_end()
+    assert st == _abi.KG_ERR_INVALID_ARG
+    assert b"capture" in _abi.lib().kg_last_error()
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", ["c64", "c128"])
 def test_static_entry_point_matches_the_workspace_entry_point(prec):
