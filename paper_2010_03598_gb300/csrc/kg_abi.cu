@@ -33,7 +33,7 @@ kg_status cuda_fail(cudaError_t e, const char* what) {
 size_t align_up(size_t x) { return (x + kg::kAlign - 1) / kg::kAlign * kg::kAlign; }
 
 struct Layout {
-  size_t ctrl = 0, bar = 0, red = 0, scal = 0, G = 0, nrm = 0, prof = 0, Gi = 0, tint = 0;
+  size_t ctrl = 0, bar = 0, iring = 0, red = 0, scal = 0, G = 0, nrm = 0, prof = 0, Gi = 0, tint = 0;
   size_t basis = 0, traj = 0, seg = 0, chi = 0, wbuf = 0, xbuf = 0;
   size_t st_u = 0, st_psi0 = 0, st_target = 0, st_fid = 0, st_grad = 0;
   size_t total = 0;
@@ -86,8 +86,9 @@ Layout make_layout(const kg_chain* ch, const kg_options* o) {
     off = align_up(off + bytes);
     return at;
   };
-  l.ctrl = take(64);   // status words and barrier counter share one memset block
+  l.ctrl = take(kg::kCtrlBytes);  // status words, barrier counter and sum ring share one memset block
   l.bar = l.ctrl + 32;
+  l.iring = l.ctrl + 64;
   l.red = take(sizeof(double) * 2 * kg::kMaxCtas * kg::kNRed);
   l.scal = take(sizeof(double) * kg::kScCount);
   l.prof = take(sizeof(long long) * 8);
@@ -292,10 +293,11 @@ static kg_status enqueue(kg_handle* h, const double* u, const void* psi0, const 
   p.red = (double*)(ws + h->lay.red);
   p.red_stride = kg::kMaxCtas;
   p.ctrl = (int*)(ws + h->lay.ctrl);
+  p.iring = (unsigned long long*)(ws + h->lay.iring);
   p.wait_limit_ns = g_wait_limit_ns.load();
   p.debug_fault = g_debug_fault.exchange(0);
   p.prof = (o.flags & KG_FLAG_PHASE_TIMING) ? (long long*)(ws + h->lay.prof) : nullptr;
-  cudaError_t e = cudaMemsetAsync(ws + h->lay.ctrl, 0, 64, h->stream);
+  cudaError_t e = cudaMemsetAsync(ws + h->lay.ctrl, 0, kg::kCtrlBytes, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(control block)");
   e = kg::launch_eval_kernel(o.prec, h->variant, p, h->ctas, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the evaluation kernel");

@@ -34,6 +34,14 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ void red_relaxed_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
@@ -154,6 +162,150 @@ __device__ __forceinline__ void tmem_st8c(uint32_t taddr, const float2 (&v)[8]) 
       : "memory");
 }
 
+// 8 FP32 values (8 columns) of this thread's TMEM row, stored and loaded with a wait.
+__device__ __forceinline__ void tmem_st8f(uint32_t taddr, const float (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n"
+      "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8f(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Split tensor-memory accesses: tmem_ld16_issue starts two 16-column loads (v and H v of a
+// tile) and returns the registers they fill; tmem_ld_wait waits for them and passes the same
+// registers through, so that no instruction can read them before the wait.  tmem_st16x2_nowait
+// starts two stores and leaves their completion to a later tmem_st_wait (before the columns are
+// read again or freed).
+struct TmemRaw32 {
+  uint32_t r[32];
+};
+__device__ __forceinline__ TmemRaw32 tmem_ld16_issue(uint32_t ta, uint32_t tb) {
+  TmemRaw32 t;
+  uint32_t* r = t.r;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%33];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta), "r"(tb)
+      : "memory");
+  return t;
+}
+__device__ __forceinline__ void tmem_ld_wait(TmemRaw32& t, float2 (&a)[8], float2 (&b)[8]) {
+  uint32_t* r = t.r;
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                 "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]),
+                 "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    b[i] = make_float2(__uint_as_float(r[16 + 2 * i]), __uint_as_float(r[16 + 2 * i + 1]));
+  }
+}
+__device__ __forceinline__ void tmem_st16x2_nowait(uint32_t ta, uint32_t tb, const float2 (&a)[8],
+                                                   const float2 (&b)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17};\n"
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], {%18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
+      "%31, %32, %33};\n" ::"r"(ta),
+      "r"(tb), "r"(__float_as_uint(a[0].x)), "r"(__float_as_uint(a[0].y)), "r"(__float_as_uint(a[1].x)),
+      "r"(__float_as_uint(a[1].y)), "r"(__float_as_uint(a[2].x)), "r"(__float_as_uint(a[2].y)),
+      "r"(__float_as_uint(a[3].x)), "r"(__float_as_uint(a[3].y)), "r"(__float_as_uint(a[4].x)),
+      "r"(__float_as_uint(a[4].y)), "r"(__float_as_uint(a[5].x)), "r"(__float_as_uint(a[5].y)),
+      "r"(__float_as_uint(a[6].x)), "r"(__float_as_uint(a[6].y)), "r"(__float_as_uint(a[7].x)),
+      "r"(__float_as_uint(a[7].y)), "r"(__float_as_uint(b[0].x)), "r"(__float_as_uint(b[0].y)),
+      "r"(__float_as_uint(b[1].x)), "r"(__float_as_uint(b[1].y)), "r"(__float_as_uint(b[2].x)),
+      "r"(__float_as_uint(b[2].y)), "r"(__float_as_uint(b[3].x)), "r"(__float_as_uint(b[3].y)),
+      "r"(__float_as_uint(b[4].x)), "r"(__float_as_uint(b[4].y)), "r"(__float_as_uint(b[5].x)),
+      "r"(__float_as_uint(b[5].y)), "r"(__float_as_uint(b[6].x)), "r"(__float_as_uint(b[6].y)),
+      "r"(__float_as_uint(b[7].x)), "r"(__float_as_uint(b[7].y))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st8c_nowait(uint32_t taddr, const float2 (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};\n" ::"r"(taddr),
+      "r"(__float_as_uint(v[0].x)), "r"(__float_as_uint(v[0].y)), "r"(__float_as_uint(v[1].x)),
+      "r"(__float_as_uint(v[1].y)), "r"(__float_as_uint(v[2].x)), "r"(__float_as_uint(v[2].y)),
+      "r"(__float_as_uint(v[3].x)), "r"(__float_as_uint(v[3].y)), "r"(__float_as_uint(v[4].x)),
+      "r"(__float_as_uint(v[4].y)), "r"(__float_as_uint(v[5].x)), "r"(__float_as_uint(v[5].y)),
+      "r"(__float_as_uint(v[6].x)), "r"(__float_as_uint(v[6].y)), "r"(__float_as_uint(v[7].x)),
+      "r"(__float_as_uint(v[7].y))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// Three 16-column loads of this thread's TMEM row (8 complex64 values each) under one wait.
+__device__ __forceinline__ void tmem_ld8c_x3(uint32_t ta, uint32_t tb, uint32_t tc, float2 (&a)[8], float2 (&b)[8],
+                                             float2 (&c)[8]) {
+  uint32_t r[48];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%48];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%49];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, "
+      "%46, %47}, [%50];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+      : "r"(ta), "r"(tb), "r"(tc)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    b[i] = make_float2(__uint_as_float(r[16 + 2 * i]), __uint_as_float(r[16 + 2 * i + 1]));
+    c[i] = make_float2(__uint_as_float(r[32 + 2 * i]), __uint_as_float(r[32 + 2 * i + 1]));
+  }
+}
+// Two 16-column stores under one wait.
+__device__ __forceinline__ void tmem_st8c_x2(uint32_t ta, uint32_t tb, const float2 (&a)[8], const float2 (&b)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17};\n"
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], {%18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
+      "%31, %32, %33};\n"
+      "tcgen05.wait::st.sync.aligned;\n" ::"r"(ta),
+      "r"(tb), "r"(__float_as_uint(a[0].x)), "r"(__float_as_uint(a[0].y)), "r"(__float_as_uint(a[1].x)),
+      "r"(__float_as_uint(a[1].y)), "r"(__float_as_uint(a[2].x)), "r"(__float_as_uint(a[2].y)),
+      "r"(__float_as_uint(a[3].x)), "r"(__float_as_uint(a[3].y)), "r"(__float_as_uint(a[4].x)),
+      "r"(__float_as_uint(a[4].y)), "r"(__float_as_uint(a[5].x)), "r"(__float_as_uint(a[5].y)),
+      "r"(__float_as_uint(a[6].x)), "r"(__float_as_uint(a[6].y)), "r"(__float_as_uint(a[7].x)),
+      "r"(__float_as_uint(a[7].y)), "r"(__float_as_uint(b[0].x)), "r"(__float_as_uint(b[0].y)),
+      "r"(__float_as_uint(b[1].x)), "r"(__float_as_uint(b[1].y)), "r"(__float_as_uint(b[2].x)),
+      "r"(__float_as_uint(b[2].y)), "r"(__float_as_uint(b[3].x)), "r"(__float_as_uint(b[3].y)),
+      "r"(__float_as_uint(b[4].x)), "r"(__float_as_uint(b[4].y)), "r"(__float_as_uint(b[5].x)),
+      "r"(__float_as_uint(b[5].y)), "r"(__float_as_uint(b[6].x)), "r"(__float_as_uint(b[6].y)),
+      "r"(__float_as_uint(b[7].x)), "r"(__float_as_uint(b[7].y))
+      : "memory");
+}
+
 // ---------------------------------------------------------------- group context
 // A group is the set of CTAs that cooperate on one problem.  All CTAs of a group are
 // co-resident (cooperative launch), execute the same sequence of barriers/reductions,
@@ -168,6 +320,8 @@ struct Group {
   int skip_arrival;          // fault injection: do not arrive at the next barrier (then cleared)
   unsigned long long epoch;  // barriers passed so far (identical in every CTA of the group)
   int stride;                // reduction slots per parity (>= size)
+  unsigned long long* iring; // fixed-point sum ring of the group ([kIRing][4], zeroed at launch), or null
+  unsigned iseq;             // fixed-point reductions so far (identical in every CTA of the group)
 };
 
 struct SmemRed {
@@ -460,6 +614,233 @@ __device__ __forceinline__ bool reduce_ff_arrive_shared(Group& g, SmemRed& sm, f
   if (size > 1) return group_barrier_shared(g, sm);
   __syncthreads();
   return ld_volatile_i32(g.ctrl + kCtrlAbort) == 0;
+}
+
+// ---------------------------------------------------------------- fixed-point group sums
+// Sums over the CTAs of a group by integer atomics.  Every CTA rounds its float-float partial to
+// a 64-bit fixed-point number q = round(x 2^S) (S chosen per slice from a bound of the sums, the
+// same in every CTA) and adds it into a ring slot in L2.  Integer addition is associative, so the
+// total has the same bits whatever the order in which the CTAs arrive, and reading it back after
+// the barrier is one load instead of a sum over every CTA's slot.  Reduction t uses slot
+// t % kIRing (three sums and a count of partials out of range); rank 0 clears slot
+// (t + 2) % kIRing as it arrives: every CTA read that slot before it arrived at the barrier that
+// followed it, and nobody adds into it before the barrier after this one.
+
+// q = round(x 2^S) for the float-float partial s (scale = 2^S, a power of two, so the products
+// are exact); `bad` is set, and 0 returned, where |x| 2^S reaches 2^61 (or x is not finite).
+__device__ __forceinline__ long long ff_to_fix(FF s, float scale, unsigned& bad) {
+  const float a = s.hi * scale, b = s.lo * scale;
+  if (!(fabsf(a) < 2.0e18f)) {
+    bad = 1u;
+    return 0;
+  }
+  return __float2ll_rn(a) + __float2ll_rn(b);
+}
+// The fixed-point total q 2^-S as a float-float (about 48 of its bits).
+__device__ __forceinline__ FF fix_to_ff(long long q, float inv_scale) {
+  const float h = __ll2float_rn(q);
+  const float l = __ll2float_rn(q - __float2ll_rn(h));  // exact remainder, rounded once more
+  return {h * inv_scale, l * inv_scale};
+}
+
+// Group barrier of a Group in shared memory that also counts a fixed-point reduction.
+__device__ __forceinline__ bool group_barrier_fix(Group& g, SmemRed& sm) {
+  __syncthreads();  // every thread has read g.iseq; every partial of this CTA has been added
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    g.iseq++;
+    if (g.skip_arrival) {
+      g.skip_arrival = 0;
+    } else {
+      red_release_add_u64(g.bar, 1ull);
+    }
+    g.epoch++;
+    const unsigned long long goal = g.epoch * (unsigned long long)g.size;
+    unsigned long long t0 = 0;
+    unsigned polls = 0;
+    while (ld_acquire_u64(g.bar) < goal) {
+      if ((++polls & 31u) == 0u) {
+        if (ld_volatile_i32(g.ctrl + kCtrlAbort)) { ok = 0; break; }
+        const unsigned long long now = globaltimer_ns();
+        if (t0 == 0) {
+          t0 = now;
+        } else if ((long long)(now - t0) > g.wait_limit_ns) {
+          atomicCAS(g.ctrl + kCtrlStatus, 0, (int)KG_ERR_TIMEOUT);
+          atomicExch(g.ctrl + kCtrlAbort, 1);
+          ok = 0;
+          break;
+        }
+        if (polls > 4096u) __nanosleep(64);
+      }
+    }
+    sm.flag = ok;
+  }
+  __syncthreads();
+  return sm.flag != 0;
+}
+
+// Group sums of NV (<= 3) per-thread float values: warp sums in float, the CTA partial in
+// float-float, the group total in fixed point (scale = 2^S).  Single-CTA groups keep the CTA's
+// float-float partials in sm.cta_ff instead.  Returns false if the group aborted.
+template <int NV>
+__device__ __forceinline__ bool reduce_fix_arrive_shared(Group& g, SmemRed& sm, float (&vals)[NV], float scale) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
+  }
+  __syncthreads();
+  const int size = g.size;
+  const unsigned slot = g.iseq % (unsigned)kIRing;
+  if (warp < NV) {
+    FF s{(lane < nw) ? sm.warp_part_f[lane * kNRed + warp] : 0.f, 0.f};
+    s = ff_warp_sum(s);
+    if (lane == 0) {
+      if (size > 1) {
+        unsigned bad = 0u;
+        const long long q = ff_to_fix(s, scale, bad);
+        unsigned long long* r = g.iring + 4u * slot;
+        red_relaxed_add_u64(r + warp, (unsigned long long)q);
+        if (bad) red_relaxed_add_u64(r + 3, 1ull);
+      } else {
+        sm.cta_ff[warp] = make_float2(s.hi, s.lo);
+      }
+    }
+  }
+  if (size > 1) {
+    if (threadIdx.x == 32 * NV && g.rank == 0) {
+      unsigned long long* z = g.iring + 4u * ((slot + 2u) % (unsigned)kIRing);
+      __stcg(z, 0ull);
+      __stcg(z + 1, 0ull);
+      __stcg(z + 2, 0ull);
+      __stcg(z + 3, 0ull);
+    }
+    return group_barrier_fix(g, sm);
+  }
+  __syncthreads();
+  return ld_volatile_i32(g.ctrl + kCtrlAbort) == 0;
+}
+
+// The same reduction split at its barrier: reduce_fix_arrive adds this CTA's partials and
+// arrives (nothing waits), so that the CTA can do work of its own -- which must not read what
+// other CTAs write before this barrier -- until group_wait_fix waits for every other arrival.
+template <int NV>
+__device__ __forceinline__ void reduce_fix_arrive(Group& g, SmemRed& sm, float (&vals)[NV], float scale) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
+  }
+  __syncthreads();
+  const int size = g.size;
+  const unsigned slot = g.iseq % (unsigned)kIRing;
+  if (warp < NV) {
+    FF s{(lane < nw) ? sm.warp_part_f[lane * kNRed + warp] : 0.f, 0.f};
+    s = ff_warp_sum(s);
+    if (lane == 0) {
+      if (size > 1) {
+        unsigned bad = 0u;
+        const long long q = ff_to_fix(s, scale, bad);
+        unsigned long long* r = g.iring + 4u * slot;
+        red_relaxed_add_u64(r + warp, (unsigned long long)q);
+        if (bad) red_relaxed_add_u64(r + 3, 1ull);
+      } else {
+        sm.cta_ff[warp] = make_float2(s.hi, s.lo);
+      }
+    }
+  }
+  if (size > 1 && threadIdx.x == 32 * NV && g.rank == 0) {
+    unsigned long long* z = g.iring + 4u * ((slot + 2u) % (unsigned)kIRing);
+    __stcg(z, 0ull);
+    __stcg(z + 1, 0ull);
+    __stcg(z + 2, 0ull);
+    __stcg(z + 3, 0ull);
+  }
+  __syncthreads();  // every thread has read g.iseq; every partial of this CTA has been added
+  if (threadIdx.x == 0) {
+    g.iseq++;
+    if (size > 1) {
+      if (g.skip_arrival) {  // injected fault: this CTA never joins; its own wait runs out too
+        g.skip_arrival = 0;
+      } else {
+        red_release_add_u64(g.bar, 1ull);
+      }
+      g.epoch++;
+    }
+  }
+}
+// Every thread: wait for the barrier reduce_fix_arrive arrived at (bounded, as group_barrier);
+// false if the group aborted or the wait ran out.
+__device__ __forceinline__ bool group_wait_fix(Group& g, SmemRed& sm) {
+  __syncthreads();  // thread 0 has arrived; every thread has read g
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (g.size > 1) {
+      const unsigned long long goal = g.epoch * (unsigned long long)g.size;
+      unsigned long long t0 = 0;
+      unsigned polls = 0;
+      while (ld_acquire_u64(g.bar) < goal) {
+        if ((++polls & 31u) == 0u) {
+          if (ld_volatile_i32(g.ctrl + kCtrlAbort)) { ok = 0; break; }
+          const unsigned long long now = globaltimer_ns();
+          if (t0 == 0) {
+            t0 = now;
+          } else if ((long long)(now - t0) > g.wait_limit_ns) {
+            atomicCAS(g.ctrl + kCtrlStatus, 0, (int)KG_ERR_TIMEOUT);
+            atomicExch(g.ctrl + kCtrlAbort, 1);
+            ok = 0;
+            break;
+          }
+          if (polls > 4096u) __nanosleep(64);
+        }
+      }
+    } else if (ld_volatile_i32(g.ctrl + kCtrlAbort)) {
+      ok = 0;
+    }
+    sm.flag = ok;
+  }
+  __syncthreads();
+  return sm.flag != 0;
+}
+
+// Totals of the group's last fixed-point reduction (thread 0, after its barrier), in two parts
+// so that the L2 load can be issued early and its result used late: fix_load reads the slot's
+// four words, fix_totals turns them into float-float values (false if a partial was out of
+// range).  Single-CTA groups: the CTA's own partials.
+struct FixRaw {
+  unsigned long long w[4];
+};
+__device__ __forceinline__ FixRaw fix_load(const Group& g) {
+  FixRaw r{{0ull, 0ull, 0ull, 0ull}};
+  if (g.size > 1) {
+    const unsigned long long* s = g.iring + 4u * ((g.iseq - 1u) % (unsigned)kIRing);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) r.w[v] = __ldcg(s + v);  // weak: the barrier's acquire ordered it
+  }
+  return r;
+}
+// The same four words copied into shared memory by an asynchronous copy (cp.async, two 16-byte
+// pieces; the caller commits and waits), so that no register holds them meanwhile.
+__device__ __forceinline__ void fix_load_async(const Group& g, FixRaw* dst) {
+  const unsigned long long* s = g.iring + 4u * ((g.iseq - 1u) % (unsigned)kIRing);
+  cp_async16(&dst->w[0], s);
+  cp_async16(&dst->w[2], s + 2);
+}
+template <int NV>
+__device__ __forceinline__ bool fix_totals(const Group& g, const SmemRed& sm, const FixRaw& r, float inv_scale,
+                                           FF (&out)[NV]) {
+  if (g.size == 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = FF{sm.cta_ff[v].x, sm.cta_ff[v].y};
+    return true;
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = fix_to_ff((long long)r.w[v], inv_scale);
+  return r.w[3] == 0ull;
 }
 
 // ---------------------------------------------------------------- small exponential

@@ -36,7 +36,7 @@ constexpr int kLogNT = 9;  // log2(kThreads)
 // Lanczos loop of a kernel: generic (any tile, complex64 or complex128), complex64 resident
 // (4096-amplitude tiles, two per CTA, on chip), complex64 streaming (4096-amplitude tiles
 // that do not stay on chip).
-enum { kModeGeneric = 0, kModeResident64 = 1, kModeStream64 = 2 };
+enum { kModeGeneric = 0, kModeResident64 = 1, kModeStream64 = 2, kModeResident64b = 3 };
 static_assert((1 << kLogNT) == kThreads, "kLogNT must match kThreads");
 
 constexpr int kSlotRanks = 256;  // groups up to this size prefetch their reduction slots
@@ -59,6 +59,7 @@ struct ResCtx {
   unsigned maskL1, mk;
   int L1, hs, hcsx, n_own, m;
   float hxy, qz, cusx, cusz, amax, bmax, bdtol;
+  float fscale, finv;  // fixed-point scale 2^S of the slice's group sums, and 2^-S
 };
 
 struct SmemSlice {
@@ -88,6 +89,7 @@ struct SmemSlice {
   Group grp;  // the group's barrier state while the resident loop runs (written by thread 0)
   float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
   float4 slotbuf[2 * kSlotRanks];  // the group's reduction slots, prefetched by warp 0
+  FixRaw fixraw;                   // the fixed-point totals of the last step (lanczos_res64b)
   unsigned ff_e_set;
   uint32_t tmem_base;
 };
@@ -1443,6 +1445,402 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
   return true;
 }
 
+// Complex64 helpers of the pair layout: a float4 holds the amplitude pair (2P, 2P + 1).
+__device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float4 pair4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ float4 ldv4(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ void stv4(float4* p, float4 v) { __stcg(p, v); }
+
+// Cross-tile part of H W for one tile in the pair layout (table entries i0 .. i1), added into h:
+// h[a] += sum wgt W[partner] for the own amplitude a = 2g + x at pair tid + 512 g.  A whole-tile
+// entry feeds every own pair, element for element; a half entry (the bond between the top
+// in-tile bit and the lowest tile bit) feeds the own half (bit 11 = bit 1 of g) from pairs
+// tid + 512 g' of the 1024-pair half block.  Two entries in flight.
+__device__ __forceinline__ void partner_acc(const SmemSlice& ss, const float2* pv, int i0, int i1, float2 (&h)[8]) {
+  constexpr int G = 2;
+  const int tid = threadIdx.x;
+  const float hxy = ss.r.hxy, cu_sx = ss.r.cusx;
+  for (int ib = i0; ib < i1; ib += G) {
+    float4 q[G][4];
+    float wq[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int i = ib + u;
+      const unsigned e = (i < i1) ? ss.ctab[i] : 0u;
+      // own pairs g fed by this entry: all four, or the half (g >> 1) == own half
+      const unsigned hm = (i >= i1) ? 0u : ((e & 4u) ? 0xfu : (((e >> 1) & 1u) ? 0xcu : 0x3u));
+      wq[u] = (e & 1u) ? cu_sx : hxy;
+      const float4* sb = reinterpret_cast<const float4*>(pv + ((size_t)(e >> 3) << 11)) + tid;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int gs = (e & 4u) ? g : (g & 1);  // a half block holds pairs tid + 512 g' (g' = g & 1)
+        q[u][g] = ((hm >> g) & 1u) ? ldv4(sb + 512 * gs) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        h[2 * g] = f2fma(f2(wq[u]), lo2(q[u][g]), h[2 * g]);
+        h[2 * g + 1] = f2fma(f2(wq[u]), hi2(q[u][g]), h[2 * g + 1]);
+      }
+  }
+}
+
+// In-tile part of H_j W for the own pairs of tile cc, from shared memory only: the bonds inside
+// the tile (times Jxy/2), the diagonal (formed once per slice) and an Sx control inside the tile;
+// parked in tensor memory at tP + 16 cc (the store is not waited for here).  Index bits of an
+// own amplitude: bit 0 = x, bits 1..9 = tid, bits 10, 11 = g.  Bonds:
+//   bond 0 (bits 0, 1): the element x = 1 - (tid & 1) of each pair, partner element tid & 1 of
+//     pair tid ^ 1;
+//   bonds 1..8 (tid bits b-1, b): pair tid ^ (3 << (b-1)), both elements;
+//   bond 9 (tid bit 8, g bit 0): pair (tid ^ 256) + 512 (g ^ 1) where they differ;
+//   bond 10 (g bits 0, 1): own pair g ^ 3 for g = 1, 2 (registers).
+// An Sx control on site 1 (bit 0) couples the two elements of an own pair (registers).
+__device__ __forceinline__ void stencil_park(const SmemSlice& ss, int cc, uint32_t tP) {
+  constexpr int T = 4096;
+  const int tid = threadIdx.x;
+  const float4* sw4 = reinterpret_cast<const float4*>(ss.r.sw + cc * T);
+  const float2* sw2 = ss.r.sw + cc * T;
+  float2 h[8];
+  {
+    const unsigned xt = (unsigned)(tid ^ (tid >> 1));
+    const float ma = (float)(tid & 1), mb = 1.f - ma;  // bond 0 feeds element 0 <=> tid odd
+    float2 b0[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) b0[g] = sw2[2 * ((tid ^ 1) + 512 * g) + (tid & 1)];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      h[2 * g] = f2mul(f2(ma), b0[g]);
+      h[2 * g + 1] = f2mul(f2(mb), b0[g]);
+    }
+#pragma unroll
+    for (int b = 1; b <= 8; ++b) {
+      if ((xt >> (b - 1)) & 1u) {
+        const float4* ps = sw4 + (tid ^ (3 << (b - 1)));
+        float4 pv4[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) pv4[g] = ps[512 * g];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          h[2 * g] = f2add(h[2 * g], lo2(pv4[g]));
+          h[2 * g + 1] = f2add(h[2 * g + 1], hi2(pv4[g]));
+        }
+      }
+    }
+    const int t8 = (tid >> 8) & 1;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (t8 != (g & 1)) {
+        const float4 pv4 = sw4[(tid ^ 256) + 512 * (g ^ 1)];
+        h[2 * g] = f2add(h[2 * g], lo2(pv4));
+        h[2 * g + 1] = f2add(h[2 * g + 1], hi2(pv4));
+      }
+    }
+  }
+  const float cu_sx = ss.r.cusx, hxy = ss.r.hxy;
+  const bool hc_sx = ss.r.hcsx != 0;
+  const int hs = ss.r.hs;
+  const float2* dg = reinterpret_cast<const float2*>(ss.r.ring) + cc * (T / 2);
+  float4 wp[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) wp[g] = sw4[tid + 512 * g];
+  // bond 10 (g bits 0, 1): g = 1 <-> g = 2
+  h[2] = f2add(h[2], lo2(wp[2]));
+  h[3] = f2add(h[3], hi2(wp[2]));
+  h[4] = f2add(h[4], lo2(wp[1]));
+  h[5] = f2add(h[5], hi2(wp[1]));
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const float2 d = dg[tid + 512 * g];
+    h[2 * g] = f2fma(f2(d.x), lo2(wp[g]), f2mul(f2(hxy), h[2 * g]));
+    h[2 * g + 1] = f2fma(f2(d.y), hi2(wp[g]), f2mul(f2(hxy), h[2 * g + 1]));
+  }
+  if (hc_sx && hs < 12) {  // the Sx control inside the tile
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      float4 q;
+      if (hs == 0) q = make_float4(wp[g].z, wp[g].w, wp[g].x, wp[g].y);
+      else if (hs <= 9) q = sw4[(tid ^ (1 << (hs - 1))) + 512 * g];
+      else q = (hs == 10) ? wp[g ^ 1] : wp[g ^ 2];
+      h[2 * g] = f2fma(f2(cu_sx), lo2(q), h[2 * g]);
+      h[2 * g + 1] = f2fma(f2(cu_sx), hi2(q), h[2 * g + 1]);
+    }
+  }
+  tmem_st8c_nowait(tP + 16u * cc, h);
+}
+
+// Near an invariant subspace (the identity for b_k^2 cancels): ||W_k - alpha_{k-1} v_{k-1}||^2
+// over the group, explicitly, then b_k and the scalars of step k (lanczos_res64b, pair layout).
+// Out of line: it runs rarely and keeps its registers out of the step loop.
+__device__ __noinline__ bool res64b_explicit_norm(SmemSlice& ss, uint32_t tV, int k) {
+  constexpr int T = 4096;
+  const int tid = threadIdx.x;
+  float n1[1] = {0.f};
+  const float ra = ss.f_alpha;
+  for (int c2 = 0; c2 < ss.r.n_own; ++c2) {
+    float2 vp[8];
+    tmem_ld8c(tV + 16u * c2, vp);
+    const float4* s4 = reinterpret_cast<const float4*>(ss.r.sw + c2 * T);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const float4 wq4 = s4[tid + 512 * g];
+      const float2 r0 = f2fma(f2(-ra), vp[2 * g], lo2(wq4));
+      const float2 r1 = f2fma(f2(-ra), vp[2 * g + 1], hi2(wq4));
+      n1[0] += r0.x * r0.x + r0.y * r0.y + r1.x * r1.x + r1.y * r1.y;
+    }
+  }
+  if (!reduce_ff_arrive_shared<1>(ss.grp, ss.red, n1)) return false;
+  if (tid < 32) {
+    FF o1[1];
+    reduce_ff_collect<1>(ss.grp, ss.red, o1);
+    if (tid == 0) {
+      ss.ff_e[k - 1] = make_float2(o1[0].hi, o1[0].lo);
+      ss.ff_e_set |= 1u << (k - 1);
+      lzf_finish_step(ss, k - 1, false, o1[0], ss.r.bdtol, ss.r.amax, ss.r.bmax);
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Lanczos loop of one slice for complex64 tiles of 4096 amplitudes, two per CTA, resident: the
+// algebra and storage of lanczos_res64 (stencil on the raw vector W_k, H v_k by its two-term
+// recurrence, basis slots holding W_k, v_{k-1} and H v_{k-1} in tensor memory, W_k of the own
+// tiles in shared memory), in the pair layout -- thread tid owns the amplitude pairs
+// P = tid + 512 g (g < 4) of each own tile, amplitudes 2P and 2P + 1, so that every vector access
+// moves 16 bytes -- with the group barrier split in two and group sums in fixed point.  Step k:
+//   1. (W_k is visible to the group; the in-tile part of H W_k is parked in tensor memory)
+//      thread 0 starts an asynchronous copy of the previous step's totals;
+//   2. both tiles: H W_k = the parked in-tile part + the partner blocks of W_k from other tiles
+//      (plain L2 loads, two table entries in flight);
+//   3. thread 0 forms alpha_{k-1}, b_k (float-float) and the scalars of step k; block barrier;
+//   4. both tiles: v_k, H v_k, W_{k+1} (shared memory and basis slot k+1), partial sums;
+//   5. CTA partials in float-float, fixed-point group sums, arrival at the group barrier;
+//   6. while the other CTAs arrive: the in-tile part of H W_{k+1} (shared memory only; the
+//      diagonal was formed once per slice), parked in tensor memory;
+//   7. wait for the group barrier.
+// Stage 6 covers the barrier's latency and the draining of the W_{k+1} stores.  Tensor-memory
+// stores are not waited for where they are issued; one wait comes before the next loads.
+__device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, double nrm_src, double uj) {
+  const EvalParams& p = *c.p;
+  SmemSlice& ss = *c.ss;
+  constexpr int NB = 2, T = 4096;
+  const int tid = threadIdx.x;
+  const bool prof = c.prof_on && tid == 0;
+  // TMEM columns: v_{k-1} of tile cc at tV + 16 cc, H v_{k-1} at tH + 16 cc, the in-tile part
+  // of H W_k at tP + 16 cc
+  const uint32_t tV = c.tm, tH = c.tm + 32u, tP = c.tm + 64u;
+  if (tid == 0) {
+    ResCtx& r = ss.r;
+    r.tbase[0] = c.tile_base(0);
+    r.tbase[1] = (c.n_own > 1) ? c.tile_base(1) : 0;
+    r.basis = (float2*)p.basis;
+    r.D = c.D;
+    r.sw = c.sv[0];
+    r.ring = c.sv[1];  // here: the diagonal of H_j, [2 tiles][2048 pairs] float2
+    r.maskL1 = c.maskL1;
+    r.mk = (unsigned)p.hc_mask;
+    r.L1 = p.L - 1;
+    r.hs = p.hc_site;
+    r.hcsx = (p.hc_kind == KG_HC_SX_SITE) ? 1 : 0;
+    r.n_own = c.n_own;
+    r.m = p.m;
+    r.hxy = (float)(0.5 * p.Jxy);
+    r.qz = (float)(0.25 * p.Jz);
+    r.cusx = (float)(0.5 * uj * p.hc_amp);
+    r.cusz = (float)(uj * p.hc_amp);
+    r.amax = 0.f;
+    r.bmax = 0.f;
+    r.bdtol = (float)p.bd_tol;
+    // Fixed-point scale of the step sums <v|W>, ||W||^2, ||v||^2: with ||v|| = 1 and
+    // ||W_{k+1}|| = ||H v_k - b_k v_{k-1}|| <= 2 ||H_j||, every total and every CTA's share is
+    // below B = 1.5 max(1, 4 hb^2), hb a row-sum bound of ||H_j||; 2^S B stays below 2^61.
+    const float hcw = (p.hc_kind == KG_HC_SX_SITE) ? 0.5f : 0.5f * (float)__popcll(p.hc_mask);
+    const float hb = (float)(p.L - 1) * (0.5f * fabsf((float)p.Jxy) + 0.25f * fabsf((float)p.Jz)) +
+                     fabsf((float)uj) * fabsf((float)p.hc_amp) * hcw;
+    int e2 = 0;
+    frexpf(1.5f * fmaxf(1.f, 4.f * hb * hb), &e2);  // B < 2^e2
+    const int S = min(max(61 - e2, 0), 100);
+    r.fscale = ldexpf(1.f, S);
+    r.finv = ldexpf(1.f, -S);
+    ss.grp = c.g;
+    lz_init(ss, nrm_src, p.m);
+    ss.ff_e_set = 0u;
+    build_chunk_table(c, p, ss);
+  }
+  // W_0 = psi: the own pairs into shared memory; the diagonal of H_j (pair order) beside it
+  {
+    const float qz = (float)(0.25 * p.Jz), cu_sz = (float)(uj * p.hc_amp);
+    const unsigned mk = (unsigned)p.hc_mask, maskL1 = c.maskL1;
+    const bool hc_sx = (p.hc_kind == KG_HC_SX_SITE);
+    const int L1 = p.L - 1;
+    float4* sw4 = reinterpret_cast<float4*>(c.sv[0]);
+    float2* dg = reinterpret_cast<float2*>(c.sv[1]);
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) {
+      if (cc >= c.n_own) break;
+      const size_t base = c.tile_base(cc);
+      const float4* s4 = reinterpret_cast<const float4*>(src + base);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        sw4[cc * (T / 2) + tid + 512 * g] = ldv4(s4 + tid + 512 * g);
+        float dd[2];
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          const unsigned gi = (unsigned)(base + 2 * (tid + 512 * g) + x);
+          const unsigned xg = (gi ^ (gi >> 1)) & maskL1;
+          dd[x] = qz * (float)(L1 - 2 * __popc(xg));
+          if (!hc_sx) dd[x] += cu_sz * 0.5f * (float)(__popc(mk) - 2 * __popc(gi & mk));
+        }
+        dg[cc * (T / 2) + tid + 512 * g] = make_float2(dd[0], dd[1]);
+      }
+    }
+  }
+  __syncthreads();
+  if (ss.meff == 0) return true;
+  const int m = ss.r.m;
+  const int n_own = ss.r.n_own;
+  for (int cc = 0; cc < n_own; ++cc) stencil_park(ss, cc, tP);  // in-tile part of H W_0
+  const float2* vec = src;  // W_k: the vector whose partner blocks are read in step k
+  bool done = false;
+  bool redo = false;  // the step is run again after its b_k was formed explicitly
+  for (int k = 0; k < m; ++k) {
+    const bool last = (k == m - 1);
+    float2* wdst = last ? nullptr : ss.r.basis + (size_t)k * ss.r.D;  // W_{k+1}: basis slot k+1
+    // ---- 1. the previous step's totals (thread 0; the copy's latency passes under stage 2)
+    if (tid == 0 && k > 0 && !redo && ss.grp.size > 1) {
+      fix_load_async(ss.grp, &ss.fixraw);
+      cp_async_commit();
+    }
+    // ---- 2. H W_k of both tiles: the parked in-tile part plus the partner blocks, parked again
+    tmem_st_wait();
+#pragma unroll 1
+    for (int cc = 0; cc < n_own; ++cc) {
+      float2 h[8];
+      tmem_ld8c(tP + 16u * cc, h);
+      partner_acc(ss, vec, ss.ct_start[cc], ss.ct_start[cc + 1], h);
+      tmem_st8c_nowait(tP + 16u * cc, h);
+    }
+    if (prof) prof_mark(ss, 0);
+    // ---- 3. alpha_{k-1}, b_k and the scalars of step k (thread 0), one block barrier
+    if (tid == 0 && k > 0 && !redo) {
+      FF tot[3];
+      if (ss.grp.size > 1) cp_async_wait<0>();
+      if (!fix_totals<3>(ss.grp, ss.red, ss.fixraw, ss.r.finv, tot)) {
+        ss.code1 = 2;
+      } else {
+        const FF b2 = lzf_after_reduce(ss, k - 1, false, tot);
+        if (ss.code1 == 0) lzf_finish_step(ss, k - 1, false, b2, ss.r.bdtol, ss.r.amax, ss.r.bmax);
+      }
+    }
+    __syncthreads();  // the scalars of step k
+    if (k > 0 && !redo) {
+      const int code = ss.code1;
+      if (code == 2) {
+        if (tid == 0) flag_nonfinite(p);
+        return false;
+      }
+      if (code == 1) {  // near an invariant subspace: form b_k explicitly, then run step k again
+        if (!res64b_explicit_norm(ss, tV, k)) return false;
+        if (ss.stop) break;
+        redo = true;
+        --k;
+        continue;
+      }
+      if (ss.stop) break;  // breakdown: v_k does not exist
+    }
+    redo = false;
+    if (prof) prof_mark(ss, 3);
+    // ---- 4. v_k, H v_k, W_{k+1} = H v_k - b_k v_{k-1} for the own amplitudes; partial sums
+    float2 acc_a = f2(0.f), acc_n = f2(0.f), acc_q = f2(0.f);
+    {
+      const float ap = ss.f_ap, ib = ss.f_ib, bk = ss.f_bk;
+      tmem_st_wait();  // H W_k parked above
+#pragma unroll 1
+      for (int cc = 0; cc < n_own; ++cc) {
+        float4* sw4 = reinterpret_cast<float4*>(ss.r.sw + cc * T);
+        float2 vp[8], hp[8], wo[8], hw[8];
+        tmem_ld8c_x3(tP + 16u * cc, tV + 16u * cc, tH + 16u * cc, hw, vp, hp);  // vp, hp unused at k = 0
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const float4 w4 = sw4[tid + 512 * g];
+          wo[2 * g] = lo2(w4);
+          wo[2 * g + 1] = hi2(w4);
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          float2 v, hv, w;
+          if (k == 0) {
+            v = f2mul(wo[a], f2(ib));
+            hv = f2mul(hw[a], f2(ib));
+            w = hv;
+          } else {
+            v = f2mul(f2fma(f2(-ap), vp[a], wo[a]), f2(ib));
+            hv = f2mul(f2fma(f2(-ap), hp[a], hw[a]), f2(ib));
+            w = f2fma(f2(-bk), vp[a], hv);
+          }
+          acc_a = f2fma(v, w, acc_a);
+          acc_n = f2fma(w, w, acc_n);
+          acc_q = f2fma(v, v, acc_q);
+          vp[a] = v;
+          hp[a] = hv;
+          wo[a] = w;
+        }
+        if (!last) {
+          tmem_st16x2_nowait(tV + 16u * cc, tH + 16u * cc, vp, hp);
+          float4* d4 = reinterpret_cast<float4*>(wdst + ss.r.tbase[cc]);
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const float4 w4 = pair4(wo[2 * g], wo[2 * g + 1]);
+            sw4[tid + 512 * g] = w4;
+            stv4(d4 + tid + 512 * g, w4);
+          }
+        }
+      }
+    }
+    if (prof) prof_mark(ss, 1);
+    // ---- 5. group sums of step k; arrival
+    float acc[3] = {acc_a.x + acc_a.y, acc_n.x + acc_n.y, acc_q.x + acc_q.y};
+    reduce_fix_arrive<3>(ss.grp, ss.red, acc, ss.r.fscale);
+    // ---- 6. the in-tile part of H W_{k+1} while the group arrives
+    if (!last)
+      for (int cc = 0; cc < n_own; ++cc) stencil_park(ss, cc, tP);
+    // ---- 7. the group barrier
+    if (!group_wait_fix(ss.grp, ss.red)) {
+      tmem_st_wait();
+      return false;
+    }
+    if (prof) prof_mark(ss, 2);
+    vec = wdst;
+    if (last) done = true;
+  }
+  tmem_st_wait();  // every store of v_k, H v_k has completed
+  if (done) {  // the sums of the last step: alpha_{m-1}, b_m (error indicator)
+    if (tid == 0) {
+      FF tot[3];
+      if (!fix_totals<3>(ss.grp, ss.red, fix_load(ss.grp), ss.r.finv, tot)) {
+        ss.code1 = 2;
+      } else {
+        const FF b2 = lzf_after_reduce(ss, m - 1, true, tot);
+        if (ss.code1 == 0) lzf_finish_step(ss, m - 1, true, b2, ss.r.bdtol, ss.r.amax, ss.r.bmax);
+      }
+    }
+    __syncthreads();
+    if (ss.code1 == 2) {
+      if (tid == 0) flag_nonfinite(p);
+      return false;
+    }
+  }
+  c.g.phase = ss.grp.phase;  // the group state goes back to every thread's context
+  c.g.epoch = ss.grp.epoch;
+  c.g.skip_arrival = ss.grp.skip_arrival;
+  c.g.iseq = ss.grp.iseq;
+  if (tid < 32) lzf_build_T(ss, m);
+  return true;
+}
+
 // ---------------------------------------------------------------- complex64 streaming path
 // For chains whose tiles do not stay on chip (more than two 4096-amplitude tiles per CTA), every
 // Lanczos step streams each own tile through the SM.  Same recurrence and global layout as
@@ -1790,10 +2188,12 @@ __device__ __noinline__ bool krylov_slice(Ctx<V>& c, const V* src, double nrm_sr
                                           int extra, const V* psi_other, double& nrm_dst, double2& e) {
   bool ok;
   if constexpr (MODE == kModeResident64) ok = lanczos_res64(c, src, nrm_src, uj);
+  else if constexpr (MODE == kModeResident64b) ok = lanczos_res64b(c, src, nrm_src, uj);
   else if constexpr (MODE == kModeStream64) ok = lanczos_str64(c, src, nrm_src, uj);
   else ok = lanczos_generic<V, A, APT, TPC, RES>(c, src, nrm_src, uj);
   if (!ok) return false;
-  return finish_slice<V, A, APT, MODE == kModeResident64>(c, src, nrm_src, tau, dst, extra, psi_other, nrm_dst, e);
+  return finish_slice<V, A, APT, MODE == kModeResident64 || MODE == kModeResident64b>(c, src, nrm_src, tau, dst, extra,
+                                                                                     psi_other, nrm_dst, e);
 }
 
 // Another step of length tau from the Krylov basis the last krylov_slice built (the basis
@@ -1803,8 +2203,8 @@ template <class V, class A, int APT, int TPC, bool RES, int MODE>
 __device__ __noinline__ bool interior_step(Ctx<V>& c, const V* src, double nrm_src, double tau, V* dst, int extra,
                                            const V* psi_other, double2& e) {
   double nrm_dst;
-  return finish_slice<V, A, APT, MODE == kModeResident64>(c, src, nrm_src, tau, dst, extra, psi_other, nrm_dst, e,
-                                                          true);
+  return finish_slice<V, A, APT, MODE == kModeResident64 || MODE == kModeResident64b>(c, src, nrm_src, tau, dst, extra,
+                                                                                     psi_other, nrm_dst, e, true);
 }
 
 // chi_N = beta f, ||chi_N||, and G_N = 2 dt Im <chi_N|Hc|psi_N>.
@@ -1904,6 +2304,8 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
   c.g.epoch = 0;
   c.g.skip_arrival = (p.debug_fault == 1 && rank == 0) ? 1 : 0;
   c.g.stride = p.red_stride;
+  c.g.iring = p.iring;
+  c.g.iseq = 0u;
   c.ss = &ss;
   c.t = p.t_bits;
   c.tile = 1 << p.t_bits;
@@ -2077,10 +2479,11 @@ template <class V, class A, int APT, int TPC, bool RES, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_constant__ EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
-  cta_setup(ss, MODE == kModeResident64);
+  constexpr bool kTmem = (MODE == kModeResident64 || MODE == kModeResident64b);
+  cta_setup(ss, kTmem);
   unsigned lz_count = 0u;  // Lanczos ring copies consumed (stage and phase parity of the ring)
   run_eval<V, A, APT, TPC, RES, MODE>(p, blockIdx.x, gridDim.x, ss, smem_dyn, lz_count);
-  cta_teardown(ss, MODE == kModeResident64);
+  cta_teardown(ss, kTmem);
 }
 
 // Many independent problems (complex64) in one cooperative launch.  Every CTA walks its own
@@ -2169,7 +2572,7 @@ static KernelChoice choice(int t_bits) {
 static KernelChoice pick(int prec, int variant, int t_bits) {
   if (prec == KG_PREC_C128) return choice<double2, double, 4, 1, false, kModeGeneric>(t_bits);
   if (variant == kVariantGenericStream) return choice<float2, float, 8, 1, false, kModeGeneric>(t_bits);
-  if (variant == kVariantResidentFull) return choice<float2, float, 8, 2, true, kModeResident64>(t_bits);
+  if (variant == kVariantResidentFull) return choice<float2, float, 8, 2, true, kModeResident64b>(t_bits);
   if (variant == kVariantResident) return choice<float2, float, 8, 2, true, kModeGeneric>(t_bits);
   if (t_bits == 12) return choice<float2, float, 8, 1, false, kModeStream64>(t_bits);
   return choice<float2, float, 8, 1, false, kModeGeneric>(t_bits);

@@ -11,6 +11,9 @@ constexpr int kMaxL = 30;
 constexpr int kNRed = 4;           // values per reduction slot
 constexpr int kMaxCtas = 2048;     // reduction slots per group
 constexpr size_t kAlign = 256;
+constexpr int kIRing = 4;          // slots of the fixed-point sum ring (4 words each)
+constexpr size_t kCtrlBytes = 256; // control block cleared before each launch: status words (0),
+                                   // barrier counter (32), fixed-point sum ring (64)
 
 // Scalars kept in the workspace (float64 unless stated).
 enum ScalarIdx {
@@ -49,6 +52,7 @@ struct EvalParams {
   double* red;              // [2][red_stride][kNRed] reduction slots
   int red_stride;           // slots per parity (>= CTAs of the group)
   int* ctrl;                // [kCtrlStatus, kCtrlAbort]
+  unsigned long long* iring;  // [kIRing][4] fixed-point group sums (zeroed before each launch), or null
   long long wait_limit_ns;
   int debug_fault;          // 1: CTA 0 skips its arrival at the first group barrier
   int reorth;               // full CGS2 re-orthogonalisation of every Lanczos step
