@@ -107,6 +107,32 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def err_vs_oracle(args, w, F, grad):
+    """Relative error of a GPU result against the committed complex128 oracle values of the same
+    seeded workload (tests/golden, written by the oracle alone): |dF|/F and ||dg||/||g||.  None if
+    no golden covers this workload, pulse length and gradient mode."""
+    if args.grad not in ("centered", "zeroth"):
+        return None
+    stem = f"oracle_{args.workload}" if w.N == 400 and args.workload == DEFAULT_WORKLOAD else None
+    if stem is None:
+        return None
+    path = os.path.join(ROOT, "tests", "golden", stem + ".json")
+    try:
+        with open(path) as fh:
+            gd = json.load(fh)
+    except Exception:
+        return None
+    key_f, key_g = f"F_{args.grad}", f"grad_{args.grad}"
+    if key_f not in gd or gd.get("N") != w.N:
+        return None
+    import numpy as np
+    out = {"F": abs(F - gd[key_f]) / abs(gd[key_f]), "golden": f"tests/golden/{stem}.json"}
+    if grad is not None and key_g in gd:
+        g_ref = np.asarray(gd[key_g])
+        out["grad"] = float(np.linalg.norm(np.asarray(grad) - g_ref) / np.linalg.norm(g_ref))
+    return out
+
+
 def ncu_traffic(kernel_key: str):
     """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -222,7 +248,7 @@ def cpu_baseline(wname: str, w, slices: int = 1):
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
     per_eval = d["seconds"] * w.N / slices
-    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{slices} slice(s) forward + backward of the {wname} workload "
                       f"({d['seconds']:.2f} s), extrapolated x{w.N // slices} to one evaluation; "
                       "NumPy complex128, 1 thread (OMP/OpenBLAS/MKL = 1)"}
@@ -246,16 +272,19 @@ def run_reference(args):
         t0 = time.perf_counter()
         oracle.segment_forward_backward(ch, u, w.dt, w.m, psi0, f)
         times.append(time.perf_counter() - t0)
-    per_eval = statistics.mean(times) * w.N
+    step_s = statistics.mean(times)
+    per_eval = step_s * w.N
     value = 1.0 / per_eval
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": config_block(w, args.workload, "c128"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": dict(config_block(w, args.workload, "c128"), grad=args.grad, reorth=bool(args.reorth)),
+        "step": f"1 slice forward + 1 slice backward of the {w.N}-slice evaluation",
+        "extrapolated_ms_per_eval": per_eval * 1e3,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"each step = 1 slice forward + 1 slice backward of {args.workload} "
-                                   f"(mean {statistics.mean(times):.2f} s), extrapolated x{w.N}; NumPy complex128, "
+                                   f"(mean {step_s:.2f} s), extrapolated x{w.N} to one evaluation; NumPy complex128, "
                                    "1 thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -320,8 +349,9 @@ def run_ours(args):
         rep = eng.sync()
         ms = [e0.elapsed_time(e1) for e0, e1 in ev]
         fid = float(eng.fid.item())
+        grad = eng.grad[: w.N].cpu().numpy().copy() if args.grad != "none" else None
         eng.close()
-        return ms, rep, fid, t_wall
+        return ms, rep, fid, t_wall, grad
 
     gpu_id = None
     try:
@@ -333,7 +363,7 @@ def run_ours(args):
     # --- headline path (timed region sampled for clocks)
     sampler = ClockSampler(gpu_id)
     sampler.start()
-    ms, rep, fid, wall = timed(args.prec, args.steps, args.warmup)
+    ms, rep, fid, wall, grad = timed(args.prec, args.steps, args.warmup)
     clocks = sampler.stop()
     value, total_s = job_throughput(args.steps, sum(ms) / 1e3, world, max_over_ranks)
     ms_per_step = total_s * 1e3 / args.steps
@@ -350,13 +380,14 @@ def run_ours(args):
     # --- plain FP64 path, same workload
     fp64 = None
     if args.fp64_steps > 0 and args.prec != "c128":
-        ms64, rep64, fid64, _ = timed("c128", args.fp64_steps, 1)
+        ms64, rep64, fid64, _, grad64 = timed("c128", args.fp64_steps, 1)
         t64 = max_over_ranks(sum(ms64) / 1e3)
         a64 = alg_bytes(w, "c128", w.ckpt) / (statistics.mean(ms64) / 1e3) / 1e9
         fp64 = {"value": args.fp64_steps * world / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.fp64_steps,
                 "steps": args.fp64_steps, "hbm_gbs_algorithmic": a64, "hbm_frac": a64 / hbm,
                 "speedup_of_headline": value / (args.fp64_steps * world / t64),
-                "rel_diff_F_vs_headline": abs(fid - fid64) / abs(fid64)}
+                "rel_diff_F_vs_headline": abs(fid - fid64) / abs(fid64),
+                "err_vs_oracle": err_vs_oracle(args, w, fid64, grad64)}
 
     # --- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -368,7 +399,8 @@ def run_ours(args):
         cpu = cpu_baseline(args.workload, w)
         if args.grad != "centered" and cpu.get("sample"):
             cpu["sample"] += "; the oracle's centred gradient, not the timed gradient mode"
-    emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, fp64, rep, fid, wall)
+    err = err_vs_oracle(args, w, fid, grad)
+    emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, fp64, rep, fid, wall, err)
     if world > 1:
         dist.destroy_process_group()
 
@@ -383,20 +415,26 @@ def run_e2e(A, chain, w, args, dev, u, psi0, f, barrier, max_over_ranks, world):
     fh = torch.tensor(f).pin_memory()
     fid_h = torch.zeros(1, dtype=torch.float64).pin_memory()
     grad_h = torch.zeros(w.N, dtype=torch.float64).pin_memory()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     eng.evaluate_host(uh, ph, fh, fid_h, grad_h)
     torch.cuda.synchronize(dev)
     barrier()
-    t0 = time.perf_counter()
+    te_local = 0.0
     for _ in range(args.e2e_steps):
-        eng.evaluate_host(uh, ph, fh, fid_h, grad_h)
-    te = max_over_ranks(time.perf_counter() - t0)
+        flush.fill_(1)  # evict L2 between steps, as the device-timed leg does (outside the timed call)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        eng.evaluate_host(uh, ph, fh, fid_h, grad_h)  # returns after the results are on the host
+        te_local += time.perf_counter() - t0
+    te = max_over_ranks(te_local)
     eng.close()
     return {"value": args.e2e_steps * world / te, "unit": UNIT,
             "h2d_bytes_per_step": int(uh.numel() * 8 + ph.numel() * 16 + fh.numel() * 16),
-            "d2h_bytes_per_step": int(8 + grad_h.numel() * 8), "api": "kg_evaluate_host (pinned host buffers)"}
+            "d2h_bytes_per_step": int(8 + grad_h.numel() * 8), "api": "kg_evaluate_host (pinned host buffers)",
+            "l2": "flushed between steps (512 MiB write, outside the timed call)"}
 
 
-def emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, fp64, rep, fid, wall):
+def emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, fp64, rep, fid, wall, err=None):
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -407,7 +445,7 @@ def emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, f
             "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps, "fp64_path": fp64,
             "report": {k: rep[k] for k in ("krylov_err_max", "norm_final", "breakdowns", "ctas", "tile_bits",
                                            "threads")},
-            "F": fid, "wall_s_timed": wall,
+            "F": fid, "err_vs_oracle": err, "wall_s_timed": wall,
         }
         print(json.dumps(out))
 

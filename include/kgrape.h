@@ -105,7 +105,11 @@ typedef struct kg_options {
   int32_t grad;            /* kg_grad_mode */
   int32_t ckpt_every;      /* 0: keep every psi_j for the backward sweep;
                               C > 0: keep psi_0, psi_C, psi_2C, ... and psi_N, and recompute
-                              each segment forward during the backward sweep */
+                              each segment forward during the backward sweep;
+                              KG_CKPT_AUTO: keep every psi_j if that workspace fits mem_budget,
+                              else checkpoint every ceil(sqrt(N)) slices (the C that minimises
+                              the N/C + C vectors held); the choice is reported in
+                              kg_report.ckpt_every */
   int32_t tile_bits;       /* 0 = automatic; else amplitudes per tile = 2^tile_bits (6..13) */
   int32_t ctas;            /* 0 = automatic; else CTAs cooperating on the problem */
   int32_t flags;           /* KG_FLAG_* */
@@ -113,7 +117,15 @@ typedef struct kg_options {
   double breakdown_tol;    /* <= 0: 1e-12 (C128) or 1e-5 (C64); Lanczos stops when
                               b_{k+1} <= tol * max(1, max|alpha| + max b) (Alg. "Lanczos",
                               the b_j > 0 test) */
+  int64_t mem_budget;      /* with KG_CKPT_AUTO: workspace bytes the caller can give; 0 = 90 % of
+                              the memory cudaMemGetInfo reports free on the current device when
+                              kg_workspace_bytes / kg_create runs.  Ignored otherwise. */
 } kg_options;
+
+/* ckpt_every value that lets the library choose the checkpoint interval (App. B: the trajectory
+ * psi_0..psi_N is what limits the memory of the gradient).  Not combined with KG_GRAD_EXACT (the
+ * choice is then 0) nor accepted by the batched and subspace entry points. */
+#define KG_CKPT_AUTO (-1)
 
 #define KG_FLAG_HOST_STAGING 1u  /* reserve workspace for kg_evaluate_host's input/output copies */
 #define KG_FLAG_PHASE_TIMING 2u  /* record per-phase SM cycles of CTA 0 into kg_report.phase_cycles */
@@ -135,6 +147,8 @@ typedef struct kg_report {
   int32_t ctas;            /* CTAs that cooperated on the problem */
   int32_t tile_bits;       /* tile size used */
   int32_t threads;         /* threads per CTA */
+  int32_t ckpt_every;      /* checkpoint interval used (0: every psi_j kept), KG_CKPT_AUTO resolved */
+  int32_t reserved0;
   int64_t phase_cycles[8]; /* with KG_FLAG_PHASE_TIMING: SM clock cycles CTA 0 spent in
                               [0] Lanczos stage 1 (v_k, partners from other tiles),
                               [1] stage 2 (stencil inside the tile), [2] group reductions

@@ -16,6 +16,7 @@ KG_HC_SX_SITE, KG_HC_SZ_SITES = 0, 1
 KG_FLAG_HOST_STAGING = 1
 KG_FLAG_PHASE_TIMING = 2
 KG_FLAG_FULL_REORTH = 4
+KG_CKPT_AUTO = -1
 KG_STATIC_WORKSPACE_BYTES = 64 << 20
 
 
@@ -28,14 +29,16 @@ class KgChain(ctypes.Structure):
 class KgOptions(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("m", ctypes.c_int32), ("prec", ctypes.c_int32), ("grad", ctypes.c_int32),
                 ("ckpt_every", ctypes.c_int32), ("tile_bits", ctypes.c_int32), ("ctas", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("dt", ctypes.c_double), ("breakdown_tol", ctypes.c_double)]
+                ("flags", ctypes.c_int32), ("dt", ctypes.c_double), ("breakdown_tol", ctypes.c_double),
+                ("mem_budget", ctypes.c_int64)]
 
 
 class KgReport(ctypes.Structure):
     _fields_ = [("krylov_err_max", ctypes.c_double), ("norm_final", ctypes.c_double), ("beta_re", ctypes.c_double),
                 ("beta_im", ctypes.c_double), ("breakdowns", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("ctas", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 8)]
+                ("threads", ctypes.c_int32), ("ckpt_every", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("phase_cycles", ctypes.c_int64 * 8)]
 
 
 class KgBatchSchedule(ctypes.Structure):

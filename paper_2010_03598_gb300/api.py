@@ -45,7 +45,9 @@ class Options:
     prec: str = "c64"         # "c64" (complex64 state, FP64 recurrences) or "c128"
     grad: str = "centered"    # "none", "centered", "zeroth", "exact" (Gauss-Lobatto over each slice),
                               # "taylor1", "taylor2" (App. B's hierarchy; subspace engines only)
-    ckpt_every: int = 0
+    ckpt_every: int = 0       # 0: keep every psi_j; C > 0: checkpoint every C slices; -1 (KG_CKPT_AUTO):
+                              # every psi_j if the workspace fits mem_budget, else every ceil(sqrt(N))
+    mem_budget: int = 0       # bytes for KG_CKPT_AUTO (0: 90 % of the device's free memory)
     tile_bits: int = 0
     ctas: int = 0
     host_staging: bool = False
@@ -58,7 +60,7 @@ class Options:
             (_abi.KG_FLAG_PHASE_TIMING if self.phase_timing else 0) | \
             (_abi.KG_FLAG_FULL_REORTH if self.reorth else 0)
         return _abi.KgOptions(self.N, self.m, _PREC[self.prec], _GRAD[self.grad], self.ckpt_every, self.tile_bits,
-                              self.ctas, flags, self.dt, self.breakdown_tol)
+                              self.ctas, flags, self.dt, self.breakdown_tol, self.mem_budget)
 
 
 def workspace_bytes(chain: ChainSpec, opts: Options) -> int:

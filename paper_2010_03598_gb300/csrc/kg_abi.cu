@@ -62,7 +62,9 @@ kg_status check_args(const kg_chain* ch, const kg_options* o) {
   if (o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED && o->grad != KG_GRAD_ZEROTH &&
       o->grad != KG_GRAD_EXACT)
     return fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, _CENTERED, _ZEROTH or _EXACT");
-  if (o->ckpt_every < 0) return fail(KG_ERR_INVALID_ARG, "ckpt_every must be >= 0");
+  if (o->ckpt_every < 0 && o->ckpt_every != KG_CKPT_AUTO)
+    return fail(KG_ERR_INVALID_ARG, "ckpt_every must be >= 0 or KG_CKPT_AUTO");
+  if (o->mem_budget < 0) return fail(KG_ERR_INVALID_ARG, "mem_budget must be >= 0");
   if (o->grad == KG_GRAD_EXACT && o->ckpt_every > 0)
     return fail(KG_ERR_UNSUPPORTED, "KG_GRAD_EXACT keeps every slice's interior states: no checkpointing");
   if (o->tile_bits != 0 && (o->tile_bits < 1 || o->tile_bits > 13))
@@ -115,6 +117,36 @@ Layout make_layout(const kg_chain* ch, const kg_options* o) {
   }
   l.total = off;
   return l;
+}
+
+// KG_CKPT_AUTO: every psi_j kept when that workspace fits the budget, else a checkpoint every
+// ceil(sqrt(N)) slices.  `budget` 0 asks the current device for its free memory (90 % of it); with
+// no device to ask, every psi_j is kept.  Other values of ckpt_every are returned unchanged.
+int resolve_ckpt(const kg_chain* ch, const kg_options* o, size_t budget) {
+  if (o->ckpt_every != KG_CKPT_AUTO) return o->ckpt_every;
+  if (o->grad == KG_GRAD_EXACT) return 0;  // the exact gradient keeps every slice's interior states
+  kg_options full = *o;
+  full.ckpt_every = 0;
+  const size_t need = make_layout(ch, &full).total;
+  if (budget == 0) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    budget = free_b / 10 * 9;
+  }
+  if (need <= budget) return 0;
+  int C = (int)std::ceil(std::sqrt((double)o->N));
+  if (C < 1) C = 1;
+  return (C >= o->N) ? 0 : C;
+}
+
+// The options with KG_CKPT_AUTO resolved.
+kg_options resolved(const kg_chain* ch, const kg_options* o, size_t budget_override = 0) {
+  kg_options r = *o;
+  r.ckpt_every = resolve_ckpt(ch, o, budget_override ? budget_override : (size_t)o->mem_budget);
+  return r;
 }
 
 int default_tile_bits(const kg_chain* ch, const kg_options* o) {
@@ -220,16 +252,19 @@ kg_status kg_workspace_bytes(const kg_chain* chain, const kg_options* opts, size
   kg_status st = check_args(chain, opts);
   if (st != KG_OK) return st;
   if (!bytes) return fail(KG_ERR_INVALID_ARG, "bytes must not be NULL");
-  *bytes = make_layout(chain, opts).total;
+  const kg_options r = resolved(chain, opts);
+  *bytes = make_layout(chain, &r).total;
   return KG_OK;
 }
 
-kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options* opts, void* workspace,
+kg_status kg_create(kg_handle** handle, const kg_chain* chain, const kg_options* opts_in, void* workspace,
                     size_t bytes, void* cuda_stream) {
   if (!handle) return fail(KG_ERR_INVALID_ARG, "handle must not be NULL");
   *handle = nullptr;
-  kg_status st = check_args(chain, opts);
+  kg_status st = check_args(chain, opts_in);
   if (st != KG_OK) return st;
+  const kg_options ropts = resolved(chain, opts_in);
+  const kg_options* opts = &ropts;
   const Layout lay = make_layout(chain, opts);
   if (!workspace) return fail(KG_ERR_WORKSPACE, "workspace must not be NULL");
   if (((uintptr_t)workspace % kg::kAlign) != 0) return fail(KG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
@@ -340,6 +375,8 @@ kg_status kg_sync(kg_handle* h, kg_report* rep) {
     rep->ctas = h->ctas;
     rep->tile_bits = h->t_bits;
     rep->threads = kg::kThreads;
+    rep->ckpt_every = h->opts.ckpt_every;
+    rep->reserved0 = 0;
     long long pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (h->opts.flags & KG_FLAG_PHASE_TIMING) {
       e = cudaMemcpy(pc, h->ws + h->lay.prof, sizeof(pc), cudaMemcpyDeviceToHost);
@@ -446,11 +483,14 @@ kg_status static_scratch_address(int dev, void** out) {
 
 }  // namespace
 
-extern "C" kg_status kg_evaluate_static(const kg_chain* chain, const kg_options* opts, const double* u,
+extern "C" kg_status kg_evaluate_static(const kg_chain* chain, const kg_options* opts_in, const double* u,
                                         const void* psi0, const void* target, double* fid, double* grad,
                                         void* cuda_stream) {
-  kg_status st = check_args(chain, opts);
+  kg_status st = check_args(chain, opts_in);
   if (st != KG_OK) return st;
+  // KG_CKPT_AUTO chooses against the size of the static scratch
+  const kg_options ropts = resolved(chain, opts_in, KG_STATIC_WORKSPACE_BYTES);
+  const kg_options* opts = &ropts;
   if (opts->flags & KG_FLAG_HOST_STAGING)
     return fail(KG_ERR_INVALID_ARG, "kg_evaluate_static does not take KG_FLAG_HOST_STAGING");
   const Layout lay = make_layout(chain, opts);
@@ -538,6 +578,8 @@ kg_status check_batch(int B, const kg_chain* chains, const kg_options* o) {
   if (o->prec != KG_PREC_C64_F64REC) return fail(KG_ERR_UNSUPPORTED, "batched evaluation runs the complex64 path only");
   if (o->flags != 0) return fail(KG_ERR_INVALID_ARG, "batched evaluation takes no flags");
   if (o->grad == KG_GRAD_EXACT) return fail(KG_ERR_UNSUPPORTED, "batched evaluation has no KG_GRAD_EXACT");
+  if (o->ckpt_every == KG_CKPT_AUTO)
+    return fail(KG_ERR_INVALID_ARG, "batched evaluation takes an explicit ckpt_every (not KG_CKPT_AUTO)");
   if (o->tile_bits != 0 || o->ctas != 0)
     return fail(KG_ERR_INVALID_ARG, "tile_bits and ctas are set by the batch schedule, not the options");
   for (int b = 0; b < B; ++b) {

@@ -658,14 +658,16 @@ constexpr int kRecombDepth = 3;  // 3 x 64 KB: all of the resident path's shared
 
 // This thread's asynchronous copies of basis vector vk for the own tiles at rb[0..n_own):
 // amplitude pairs 2 (tid + 512 g) + {0, 1}, g < 4, into stage st[(ct * 4 + g) * kThreads + tid].
+// The basis is read once here: the copies carry an evict_first L2 policy (see l2_policy_first).
 __device__ __forceinline__ void recomb_issue(const float2* vk, const size_t (&rb)[2], int n_own, float4* st) {
   const int tid = threadIdx.x;
+  const unsigned long long pol = l2_policy_first();
 #pragma unroll
   for (int ct = 0; ct < 2; ++ct) {
     if (ct < n_own) {
 #pragma unroll
       for (int g = 0; g < 4; ++g)
-        cp_async16(st + (ct * 4 + g) * kThreads + tid, vk + rb[ct] + 2 * (size_t)(tid + g * kThreads));
+        cp_async16_hint(st + (ct * 4 + g) * kThreads + tid, vk + rb[ct] + 2 * (size_t)(tid + g * kThreads), pol);
     }
   }
 }
@@ -683,7 +685,7 @@ struct RecombConsts {
 template <class A>
 __device__ __forceinline__ void recomb_amp(const RecombConsts& rc, size_t gi, float2 y, float2* dst, int extra,
                                            const float2* psi_other, A& nacc, A& gacc, double& ex0, double& ex1) {
-  stv(dst + gi, y);
+  stv_hint(dst + gi, y, l2_policy_first());
   nacc += (A)(y.x * y.x + y.y * y.y);
   if (extra == kExtraOverlapTarget) {
     const double2 f = rc.target[gi];
@@ -1451,12 +1453,26 @@ __device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); 
 __device__ __forceinline__ float4 pair4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
 __device__ __forceinline__ float4 ldv4(const float4* p) { return __ldcg(p); }
 __device__ __forceinline__ void stv4(float4* p, float4 v) { __stcg(p, v); }
+// Stores with an L2 eviction priority.  Within a slice the L2 (about 126 MB) cannot hold the whole
+// Krylov basis at L = 20 (19 vectors of 8 MiB): the basis vectors are stored with evict_last, so
+// that as many as possible are still there when the recombination reads them; the recombination's
+// reads of the basis and the state it writes go with evict_first (l2_policy_first).
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void stv4_hint(float4* p, float4 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(pol)
+               : "memory");
+}
 
 // Cross-tile part of H W for one tile in the pair layout (table entries i0 .. i1), added into h:
-// h[a] += sum wgt W[partner] for the own amplitude a = 2g + x at pair tid + 512 g.  A whole-tile
-// entry feeds every own pair, element for element; a half entry (the bond between the top
-// in-tile bit and the lowest tile bit) feeds the own half (bit 11 = bit 1 of g) from pairs
-// tid + 512 g' of the 1024-pair half block.  Two entries in flight.
+// h[a] += wgt W[partner] for the own amplitude a = 2g + x at pair tid + 512 g.  A whole-tile entry
+// feeds every own pair, element for element; a half entry (the bond between the top in-tile bit
+// and the lowest tile bit) feeds the own half (bit 11 = bit 1 of g) from pairs tid + 512 g' of the
+// 1024-pair half block.  Two entries in flight.
 __device__ __forceinline__ void partner_acc(const SmemSlice& ss, const float2* pv, int i0, int i1, float2 (&h)[8]) {
   constexpr int G = 2;
   const int tid = threadIdx.x;
@@ -1739,10 +1755,12 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
     if (k > 0 && !redo) {
       const int code = ss.code1;
       if (code == 2) {
+        tmem_st_wait();
         if (tid == 0) flag_nonfinite(p);
         return false;
       }
       if (code == 1) {  // near an invariant subspace: form b_k explicitly, then run step k again
+        tmem_st_wait();
         if (!res64b_explicit_norm(ss, tV, k)) return false;
         if (ss.stop) break;
         redo = true;
@@ -1791,11 +1809,12 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
         if (!last) {
           tmem_st16x2_nowait(tV + 16u * cc, tH + 16u * cc, vp, hp);
           float4* d4 = reinterpret_cast<float4*>(wdst + ss.r.tbase[cc]);
+          const unsigned long long keep = l2_evict_last();
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             const float4 w4 = pair4(wo[2 * g], wo[2 * g + 1]);
             sw4[tid + 512 * g] = w4;
-            stv4(d4 + tid + 512 * g, w4);
+            stv4_hint(d4 + tid + 512 * g, w4, keep);
           }
         }
       }

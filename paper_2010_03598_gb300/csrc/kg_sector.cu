@@ -1348,6 +1348,8 @@ kg_status kg_sector_sync(kg_sector_handle* h, kg_report* rep) {
     rep->launches = 1;
     rep->ctas = h->grid;
     rep->threads = kg::sector_threads(h->opts.prec, h->basis.D);
+    rep->ckpt_every = 0;
+    rep->reserved0 = 0;
     if (h->opts.flags & KG_FLAG_PHASE_TIMING) {
       long long pc[8];
       e = cudaMemcpy(pc, h->ws + h->lay.prof, sizeof(pc), cudaMemcpyDeviceToHost);

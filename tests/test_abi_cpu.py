@@ -115,7 +115,7 @@ def test_full_reorthogonalisation_flag_is_accepted(lib):
     ({}, dict(dt=float("inf")), _abi.KG_ERR_INVALID_ARG),
     ({}, dict(prec=5), _abi.KG_ERR_INVALID_ARG),
     ({}, dict(grad=9), _abi.KG_ERR_INVALID_ARG),
-    ({}, dict(ckpt_every=-1), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(ckpt_every=-2), _abi.KG_ERR_INVALID_ARG),
     ({}, dict(tile_bits=14), _abi.KG_ERR_INVALID_ARG),
     ({}, dict(ctas=5000), _abi.KG_ERR_INVALID_ARG),
     ({}, dict(flags=8), _abi.KG_ERR_INVALID_ARG),
@@ -150,6 +150,30 @@ def test_wait_limit_and_fault_hook_arguments(lib):
     assert lib.kg_set_wait_limit_ns(2_000_000_000) == _abi.KG_OK
     assert lib.kg_debug_set_fault(3) == _abi.KG_ERR_INVALID_ARG
     assert lib.kg_debug_set_fault(0) == _abi.KG_OK
+
+
+def test_automatic_checkpoint_interval_follows_the_budget(lib):
+    # KG_CKPT_AUTO keeps every psi_j when that workspace fits the budget, and otherwise checkpoints
+    # every ceil(sqrt(N)) slices -- the interval that minimises the N/C + C vectors held.
+    C64 = _abi.KG_PREC_C64_F64REC
+    ch = _chain(L=24)
+    full = _ws(lib, ch, _opts(N=400, m=24, prec=C64, ckpt_every=0))[1]
+    c20 = _ws(lib, ch, _opts(N=400, m=24, prec=C64, ckpt_every=20))[1]
+    assert c20 < full
+    for budget, expect in ((full, full), (full - 1, c20), (1, c20)):
+        st, n = _ws(lib, ch, _opts(N=400, m=24, prec=C64, ckpt_every=_abi.KG_CKPT_AUTO, mem_budget=budget))
+        assert st == _abi.KG_OK and n == expect
+    for N, C in ((390, 20), (401, 21), (10, 4)):
+        want = _ws(lib, _chain(L=10), _opts(N=N, ckpt_every=C))[1]
+        got = _ws(lib, _chain(L=10), _opts(N=N, ckpt_every=_abi.KG_CKPT_AUTO, mem_budget=1))[1]
+        assert got == want, (N, C)
+    # the exact gradient keeps every slice's interior states: no checkpoints whatever the budget
+    ex = dict(N=40, grad=_abi.KG_GRAD_EXACT)
+    st, n = _ws(lib, _chain(L=10), _opts(ckpt_every=_abi.KG_CKPT_AUTO, mem_budget=1, **ex))
+    assert st == _abi.KG_OK and n == _ws(lib, _chain(L=10), _opts(ckpt_every=0, **ex))[1]
+    # other negative intervals and negative budgets are refused
+    assert _ws(lib, ch, _opts(ckpt_every=-2))[0] == _abi.KG_ERR_INVALID_ARG
+    assert _ws(lib, ch, _opts(ckpt_every=_abi.KG_CKPT_AUTO, mem_budget=-5))[0] == _abi.KG_ERR_INVALID_ARG
 
 
 def test_package_import_does_not_need_the_library():

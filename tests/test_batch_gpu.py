@@ -1,9 +1,12 @@
 """Batched persistent launch: many independent pulses in one cooperative kernel.
 
-Checked against the oracle (complex128) at the complex64 tolerances, against the
-single-problem path, across schedules (results must not depend on how problems are laid
-out on CTAs), and when the launch is captured in a CUDA graph.
+Checked against the oracle (complex128) at the complex64 tolerances -- in the 256-pulse workload,
+every pulse with L <= 12 -- against the single-problem path, across schedules (results must not
+depend on how problems are laid out on CTAs), and when the launch is captured in a CUDA graph.
 """
+import multiprocessing as mp
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -114,10 +117,23 @@ def test_batch_launch_in_a_cuda_graph():
     b.close()
 
 
+def _oracle_batch_pulse(i):
+    # one pulse of the 256-pulse workload, complex128 oracle (runs in a spawned worker, no GPU)
+    d = W.batch_instances()[i]
+    F, g, _ = oracle.evaluate(oracle.Chain(d["L"], 1.0, d["delta"]), d["u"], W.BATCH_DT, W.BATCH_M, d["psi0"],
+                              d["target"])
+    return i, F, g
+
+
 def test_batch256_workload_against_single_runs_and_oracle():
     A = api()
     inst = W.batch_instances()
     N, dt, m = W.BATCH_N, W.BATCH_DT, W.BATCH_M
+    # every pulse with L <= 12 against the oracle (about a hundred): computed by a pool of spawned
+    # worker processes while the GPU runs
+    small = [i for i, d in enumerate(inst) if d["L"] <= 12]
+    pool = mp.get_context("spawn").Pool(processes=max(1, min(16, os.cpu_count() or 1)))
+    pending = pool.map_async(_oracle_batch_pulse, small)
     dev = torch.device("cuda", 0)
     for d in inst:
         d["ut"] = torch.tensor(d["u"], device=dev)
@@ -136,10 +152,12 @@ def test_batch256_workload_against_single_runs_and_oracle():
         assert rel(F[i], float(fid.item())) <= TF
         assert nrel(G[i], grad.cpu().numpy()) <= TG
         eng.close()
-    # the two smallest chains against the oracle
-    small = sorted(range(len(inst)), key=lambda i: (inst[i]["L"], i))[:2]
-    for i in small:
-        d = inst[i]
-        Fr, gr, _ = oracle.evaluate(oracle.Chain(d["L"], 1.0, d["delta"]), d["u"], dt, m, d["psi0"], d["target"])
-        assert rel(F[i], Fr) <= TF, (i, F[i], Fr)
-        assert nrel(G[i], gr) <= TG, (i, nrel(G[i], gr))
+    try:
+        results = pending.get(timeout=1800)
+    finally:
+        pool.close()
+        pool.join()
+    assert len(results) == len(small) >= 90
+    for i, Fr, gr in results:
+        assert rel(F[i], Fr) <= TF, (i, inst[i]["L"], F[i], Fr)
+        assert nrel(G[i], gr) <= TG, (i, inst[i]["L"], nrel(G[i], gr))
