@@ -170,13 +170,14 @@ def test_batch256_workload_against_single_runs_and_oracle():
     assert len(results) == len(small) >= 90
     # The complex64 state carries rounding of ~1e-7 per step, so the error of beta = <f|psi_N> is
     # about ||d psi|| / sqrt(D) whatever beta is: relative to F = |beta|^2 it is amplified where the
-    # overlap is far below a random target's typical F ~ 1/D.  The relative bound 1e-5 applies where
-    # F D >= 0.1; below that (1 pulse in 100 here) the same bound is applied to 0.1 / D.
-    anomalous = 0
+    # overlap is far below a random target's typical F ~ 1/D (F D is exponentially distributed, mean 1).
+    # The relative bound 1e-5 applies where F D >= 0.2 (about 80 % of the pulses); below that the
+    # same bound is applied to 0.2 / D.
+    small_overlap = 0
     for i, Fr, gr in results:
         D = 1 << inst[i]["L"]
-        scale = max(Fr, 0.1 / D)
-        anomalous += Fr < 0.1 / D
+        scale = max(Fr, 0.2 / D)
+        small_overlap += Fr < 0.2 / D
         assert abs(F[i] - Fr) <= TF * scale, (i, inst[i]["L"], F[i], Fr, Fr * D)
         assert nrel(G[i], gr) <= TG, (i, inst[i]["L"], nrel(G[i], gr))
-    assert anomalous <= len(results) // 20
+    assert small_overlap <= len(results) // 3
