@@ -48,7 +48,7 @@ class KgBatchSchedule(ctypes.Structure):
 
 class KgSector(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("K", ctypes.c_int32), ("parity", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("hc_site_mask", ctypes.c_uint64), ("Jxy", ctypes.c_double),
+                ("block_threads", ctypes.c_int32), ("hc_site_mask", ctypes.c_uint64), ("Jxy", ctypes.c_double),
                 ("Jz", ctypes.c_double), ("hc_amp", ctypes.c_double)]
 
 

@@ -278,10 +278,12 @@ class SectorSpec:
     Jz: float = 1.0
     hc_mask: int | None = None  # default: sites 1 and L
     hc_amp: float = 1.0       # Sec. 3.1: (J/2)(sigma^z_1 + sigma^z_L) = J (Sz_1 + Sz_L)
+    block_threads: int = 0    # threads per CTA: 0 = chosen from D, or 128, 256, 512 (tune.py times them)
 
     def to_c(self) -> _abi.KgSector:
         mask = (1 | (1 << (self.L - 1))) if self.hc_mask is None else int(self.hc_mask)
-        return _abi.KgSector(self.L, self.K, self.parity, 0, mask, self.Jxy, self.Jz, self.hc_amp)
+        return _abi.KgSector(self.L, self.K, self.parity, int(self.block_threads), mask, self.Jxy, self.Jz,
+                             self.hc_amp)
 
 
 def sector_dim(spec: SectorSpec) -> int:

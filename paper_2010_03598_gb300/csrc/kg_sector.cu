@@ -870,14 +870,25 @@ static SecKernel sec_choice() {
 }
 
 // Threads and rows per thread by dimension: the smallest block that covers D with <= 8 rows per
-// thread (10 for complex64 up to 2560, which keeps two CTAs on an SM).
-static SecKernel sec_pick(int prec, int D) {
+// thread (10 for complex64 up to 2560, which keeps two CTAs on an SM); or, with nt = 128, 256 or
+// 512 threads, that block with the fewest rows per thread that covers D (nt.threads == 0: none).
+static SecKernel sec_pick(int prec, int D, int nt = 0) {
   if (prec == KG_PREC_C128) {
+    if (nt == 128) return (D <= 512) ? sec_choice<double2, 128, 4>() : SecKernel{nullptr, 0};
+    if (nt == 256) return (D <= 1024) ? sec_choice<double2, 256, 4>()
+                                      : (D <= 2048) ? sec_choice<double2, 256, 8>() : SecKernel{nullptr, 0};
+    if (nt == 512) return (D <= 4096) ? sec_choice<double2, 512, 8>() : SecKernel{nullptr, 0};
     if (D <= 512) return sec_choice<double2, 128, 4>();
     if (D <= 1024) return sec_choice<double2, 256, 4>();
     if (D <= 2048) return sec_choice<double2, 256, 8>();
     return sec_choice<double2, 512, 8>();
   }
+  if (nt == 128) return (D <= 512) ? sec_choice<float2, 128, 4>() : SecKernel{nullptr, 0};
+  if (nt == 256)
+    return (D <= 1024) ? sec_choice<float2, 256, 4>()
+                       : (D <= 2048) ? sec_choice<float2, 256, 8>()
+                                     : (D <= 2560) ? sec_choice<float2, 256, 10>() : SecKernel{nullptr, 0};
+  if (nt == 512) return (D <= 4096) ? sec_choice<float2, 512, 8>() : SecKernel{nullptr, 0};
   if (D <= 512) return sec_choice<float2, 128, 4>();
   if (D <= 1024) return sec_choice<float2, 256, 4>();
   if (D <= 2048) return sec_choice<float2, 256, 8>();
@@ -893,8 +904,9 @@ size_t sector_smem_bytes(int prec, int D, int ell) {
   return 2 * Dp * vb + (size_t)ell * D * 2;
 }
 
-cudaError_t sector_kernel_max_ctas(int prec, int D, int ell, int* out) {
-  const SecKernel k = sec_pick(prec, D);
+cudaError_t sector_kernel_max_ctas(int prec, int D, int ell, int nt, int* out) {
+  const SecKernel k = sec_pick(prec, D, nt);
+  if (!k.fn) return cudaErrorInvalidValue;
   const size_t smem = sector_smem_bytes(prec, D, ell);
   cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -906,10 +918,12 @@ cudaError_t sector_kernel_max_ctas(int prec, int D, int ell, int* out) {
   return cudaSuccess;
 }
 
-int sector_threads(int prec, int D) { return sec_pick(prec, D).threads; }
+int sector_threads(int prec, int D, int nt) { return sec_pick(prec, D, nt).threads; }
+bool sector_shape_ok(int prec, int D, int nt) { return sec_pick(prec, D, nt).fn != nullptr; }
 
-cudaError_t launch_sector_kernel(int prec, const SectorParams& p, int ctas, cudaStream_t stream) {
-  const SecKernel k = sec_pick(prec, p.D);
+cudaError_t launch_sector_kernel(int prec, const SectorParams& p, int ctas, int nt, cudaStream_t stream) {
+  const SecKernel k = sec_pick(prec, p.D, nt);
+  if (!k.fn) return cudaErrorInvalidValue;
   const size_t smem = sector_smem_bytes(prec, p.D, p.ell);
   cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -941,7 +955,8 @@ kg_status check_sector(const kg_sector* s) {
   if (s->L < 2 || s->L > kg::kMaxL) return host_fail(KG_ERR_INVALID_ARG, "L must satisfy 2 <= L <= 30");
   if (s->K < 0 || s->K > s->L) return host_fail(KG_ERR_INVALID_ARG, "K must satisfy 0 <= K <= L");
   if (s->parity < -1 || s->parity > 1) return host_fail(KG_ERR_INVALID_ARG, "parity must be -1, 0 or +1");
-  if (s->reserved0 != 0) return host_fail(KG_ERR_INVALID_ARG, "reserved0 must be 0");
+  if (s->block_threads != 0 && s->block_threads != 128 && s->block_threads != 256 && s->block_threads != 512)
+    return host_fail(KG_ERR_INVALID_ARG, "block_threads must be 0, 128, 256 or 512");
   if ((s->hc_site_mask >> s->L) != 0) return host_fail(KG_ERR_INVALID_ARG, "hc_site_mask has bits at or above L");
   if (s->parity != 0 && mirror_bits(s->hc_site_mask, s->L) != s->hc_site_mask)
     return host_fail(KG_ERR_INVALID_ARG, "a parity subspace needs a mirror-symmetric hc_site_mask");
@@ -1093,12 +1108,12 @@ kg_status check_sector_opts(const kg_options* o, int B) {
 }
 
 // Grid for B pulses: every CTA that fits co-resident, at most B, at most opts->ctas.
-kg_status sector_grid(const kg_options* o, int D, int ell, int B, int* grid) {
+kg_status sector_grid(const kg_options* o, int D, int ell, int nt, int B, int* grid) {
   const size_t smem = kg::sector_smem_bytes(o->prec, D, ell);
   if (smem > 200 * 1024)
     return host_fail(KG_ERR_UNSUPPORTED, "the subspace's state and tables exceed one CTA's shared memory");
   int maxc = 0;
-  cudaError_t e = kg::sector_kernel_max_ctas(o->prec, D, ell, &maxc);
+  cudaError_t e = kg::sector_kernel_max_ctas(o->prec, D, ell, nt, &maxc);
   if (e != cudaSuccess) {
     return host_fail(KG_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorName(e));
   }
@@ -1185,13 +1200,15 @@ kg_status kg_sector_workspace_bytes(const kg_sector* s, const kg_options* o, int
   SectorBasis b;
   std::string why;
   if (!build_basis(s, (size_t)kg::kSecMaxRows, true, b, why)) return host_fail(KG_ERR_UNSUPPORTED, why);
+  if (!kg::sector_shape_ok(o->prec, b.D, s->block_threads))
+    return host_fail(KG_ERR_INVALID_ARG, "block_threads too few for the subspace's dimension");
   // one trajectory per CTA: size for the grid kg_sector_create will choose on the current device
   // (B CTAs if no device can be queried)
   int grid = B;
   int dev = 0, maxc = 0;
   if (cudaGetDevice(&dev) == cudaSuccess &&
       kg::sector_smem_bytes(o->prec, b.D, b.ell_width) <= 200 * 1024 &&
-      kg::sector_kernel_max_ctas(o->prec, b.D, b.ell_width, &maxc) == cudaSuccess && maxc > 0) {
+      kg::sector_kernel_max_ctas(o->prec, b.D, b.ell_width, s->block_threads, &maxc) == cudaSuccess && maxc > 0) {
     grid = std::min(B, maxc);
     if (o->ctas > 0) grid = std::min(grid, o->ctas);
   } else {
@@ -1218,6 +1235,10 @@ kg_status kg_sector_create(kg_sector_handle** handle, const kg_sector* s, const 
     delete h;
     return host_fail(KG_ERR_INVALID_ARG, "the subspace is empty");
   }
+  if (!kg::sector_shape_ok(o->prec, h->basis.D, s->block_threads)) {
+    delete h;
+    return host_fail(KG_ERR_INVALID_ARG, "block_threads too few for the subspace's dimension");
+  }
   const size_t need1 = sector_layout(h->basis.D, h->basis.ell_width, o, B, 1).total;  // one CTA
   if (!workspace || ((uintptr_t)workspace % kg::kAlign) != 0 || bytes < need1) {
     delete h;
@@ -1231,7 +1252,7 @@ kg_status kg_sector_create(kg_sector_handle** handle, const kg_sector* s, const 
     return host_fail(KG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorName(e));
   }
   int grid = 1;
-  if ((st = sector_grid(o, h->basis.D, h->basis.ell_width, B, &grid)) != KG_OK) {
+  if ((st = sector_grid(o, h->basis.D, h->basis.ell_width, s->block_threads, B, &grid)) != KG_OK) {
     delete h;
     return st;
   }
@@ -1317,7 +1338,7 @@ kg_status kg_sector_evaluate(kg_sector_handle* h, const double* u, const void* p
   p.prof = (o.flags & KG_FLAG_PHASE_TIMING) ? (long long*)(ws + h->lay.prof) : nullptr;
   cudaError_t e = cudaMemsetAsync(ws + h->lay.ctrl, 0, 64, h->stream);
   if (e != cudaSuccess) return host_fail(KG_ERR_CUDA, std::string("cudaMemsetAsync(control block): ") + cudaGetErrorName(e));
-  e = kg::launch_sector_kernel(o.prec, p, h->grid, h->stream);
+  e = kg::launch_sector_kernel(o.prec, p, h->grid, h->sector.block_threads, h->stream);
   if (e != cudaSuccess) return host_fail(KG_ERR_CUDA, std::string("launch of the subspace kernel: ") + cudaGetErrorName(e));
   return KG_OK;
 }
@@ -1347,7 +1368,7 @@ kg_status kg_sector_sync(kg_sector_handle* h, kg_report* rep) {
     rep->status = ctrl[kg::kCtrlStatus];
     rep->launches = 1;
     rep->ctas = h->grid;
-    rep->threads = kg::sector_threads(h->opts.prec, h->basis.D);
+    rep->threads = kg::sector_threads(h->opts.prec, h->basis.D, h->sector.block_threads);
     rep->ckpt_every = 0;
     rep->reserved0 = 0;
     if (h->opts.flags & KG_FLAG_PHASE_TIMING) {

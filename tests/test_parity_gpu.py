@@ -4,6 +4,7 @@ Tolerances (relative; gradients normwise, since single components can be ~0):
   complex128 path:            |dF|/F <= 1e-10, ||dg||/||g|| <= 1e-10
   complex64 + FP64 recurrences: |dF|/F <= 1e-5,  ||dg||/||g|| <= 1e-4
 """
+import dataclasses
 import json
 import os
 
@@ -404,6 +405,27 @@ def test_L20_adjoint_gradient_vs_central_finite_differences():
     assert nrel(g64, g128) <= 1e-4
     assert nrel(g64[idx], fd) <= 1e-3
     e64.close()
+
+
+# ------------------------------------------------------------------ autotuned schedule
+def test_tuned_single_problem_schedule_gives_the_default_evaluation(tmp_path):
+    # The tuner times tile sizes x CTAs; whichever it keeps, the evaluation is the same to rounding
+    # (different tilings sum in another order), and the same schedule twice is bitwise equal.
+    from paper_2010_03598_gb300 import tune
+    A = api()
+    w = W.WORKLOADS["xxz_L16_N200_m20"]
+    u, psi0, f = W.instance(w, N=12)
+    chain = A.ChainSpec(w.L, w.Jxy, w.Jz)
+    opts = A.Options(12, w.dt, w.m, prec="c64")
+    ut, pt, ft = to_dev(u, psi0, f)
+    best = tune.tune_single(chain, opts, ut, pt, ft, cache_path=str(tmp_path / "tune.json"), repeats=1)
+    assert sum(t["ms"] is not None for t in best["trials"]) >= 3
+    F0, g0, _ = run_gpu(chain, opts, u, psi0, f)
+    tuned = dataclasses.replace(opts, tile_bits=best["tile_bits"], ctas=best["ctas"])
+    F1, g1, _ = run_gpu(chain, tuned, u, psi0, f)
+    F2, g2, _ = run_gpu(chain, tuned, u, psi0, f)
+    check("c64", F1, g1, F0, g0)
+    assert F1 == F2 and np.array_equal(g1, g2)
 
 
 # ------------------------------------------------------------------ automatic checkpoint interval

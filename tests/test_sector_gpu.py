@@ -272,3 +272,42 @@ def test_sector_exact_gradient_matches_the_dense_derivative():
         _, g, _ = run(A.SectorSpec(L, K, 1), A.Options(N, dt, m, prec="c128", grad=grad), u[None, :], psi0, f)
         errs[grad] = nrel(g[0], g_ex)
     assert errs["exact"] < 1e-3 * errs["centered"], errs
+
+
+def test_every_block_shape_gives_the_same_evaluation():
+    # The subspace kernel's block shape (threads per CTA; the tuner's choice) changes only the speed.
+    A = api()
+    spec = A.SectorSpec(14, 4, 1)
+    D = A.sector_dim(spec)
+    N, B = 48, 3
+    rng = np.random.default_rng(14)
+    dev = torch.device("cuda", 0)
+    u = torch.tensor(rng.uniform(-1, 1, (B, N)), device=dev)
+    e1 = torch.zeros(D, dtype=torch.complex128, device=dev)
+    e1[0] = 1
+    eD = torch.zeros(D, dtype=torch.complex128, device=dev)
+    eD[-1] = 1
+    out = {}
+    for nt in (0, 128, 256, 512):
+        import dataclasses
+        sec = A.KGrapeSector(dataclasses.replace(spec, block_threads=nt), A.Options(N, 0.5, 10, prec="c64"), B=B)
+        fid, grad = sec.evaluate(u, e1, eD)
+        rep = sec.sync()
+        assert rep["threads"] == (nt if nt else 128)
+        out[nt] = (fid.cpu().numpy().copy(), grad.cpu().numpy().copy())
+        sec.close()
+    F0, g0 = out[0]
+    for nt in (128, 256, 512):
+        F, g = out[nt]
+        assert np.all(np.abs(F - F0) <= 1e-5 * np.abs(F0)), nt
+        assert np.linalg.norm(g - g0) <= 1e-4 * np.linalg.norm(g0), nt
+
+
+def test_a_block_too_small_for_the_subspace_is_refused():
+    A = api()
+    from paper_2010_03598_gb300 import _abi
+    import dataclasses
+    spec = dataclasses.replace(A.SectorSpec(20, 4, 1), block_threads=128)  # D = 2445 > 128 x 4
+    with pytest.raises(_abi.KGrapeError) as ei:
+        A.KGrapeSector(spec, A.Options(8, 0.5, 10, prec="c64"), B=1)
+    assert ei.value.status == _abi.KG_ERR_INVALID_ARG
