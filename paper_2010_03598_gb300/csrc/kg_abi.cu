@@ -374,7 +374,7 @@ kg_status kg_sync(kg_handle* h, kg_report* rep) {
     rep->launches = h->launches;
     rep->ctas = h->ctas;
     rep->tile_bits = h->t_bits;
-    rep->threads = kg::kThreads;
+    rep->threads = kg::eval_kernel_threads(h->opts.prec, h->variant, h->t_bits);
     rep->ckpt_every = h->opts.ckpt_every;
     rep->reserved0 = 0;
     long long pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};

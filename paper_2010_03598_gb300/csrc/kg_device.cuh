@@ -10,6 +10,38 @@
 
 namespace kg {
 
+// ---------------------------------------------------------------- worker threads
+// A block holds at most kWorkMax worker threads, which share the block's data; the headline
+// kernel's blocks carry one more warp (the control warp) that serves the group sums of its
+// Lanczos loop and meets the workers only at named barriers.  wsync is the workers' block
+// barrier (named barrier 1 where a control warp exists, else the block barrier) and nwork their
+// number; every device function below that synchronises or strides by the block uses them.
+constexpr int kWorkMax = 512;
+__device__ __forceinline__ int nwork() { return blockDim.x > (unsigned)kWorkMax ? kWorkMax : (int)blockDim.x; }
+__device__ __forceinline__ void wsync() {
+  if (blockDim.x > (unsigned)kWorkMax) asm volatile("barrier.sync 1, 512;" ::: "memory");
+  else __syncthreads();
+}
+__device__ __forceinline__ bool wsync_or(bool pred) {
+  if (blockDim.x > (unsigned)kWorkMax) {
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, 1, 512, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((unsigned)pred)
+        : "memory");
+    return r != 0u;
+  }
+  return __syncthreads_or(pred) != 0;
+}
+// Named barrier `id` of `n` threads: wait for it, or only mark this warp's arrival.
+__device__ __forceinline__ void nbar_sync(int id, int n) {
+  asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int n) {
+  asm volatile("barrier.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // ---------------------------------------------------------------- vector traits
 template <class V> struct VecTraits;
 template <> struct VecTraits<float2> { using R = float; };
@@ -270,6 +302,41 @@ __device__ __forceinline__ void tmem_st8c_nowait(uint32_t taddr, const float2 (&
       "r"(__float_as_uint(v[7].y))
       : "memory");
 }
+// Half of the above: three 8-column loads (4 complex values each) under one wait, and two
+// 8-column stores without a wait.
+__device__ __forceinline__ void tmem_ld4c_x3(uint32_t ta, uint32_t tb, uint32_t tc, float2 (&a)[4], float2 (&b)[4],
+                                             float2 (&c)[4]) {
+  uint32_t r[24];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%24];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%25];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%26];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+      : "r"(ta), "r"(tb), "r"(tc)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    b[i] = make_float2(__uint_as_float(r[8 + 2 * i]), __uint_as_float(r[8 + 2 * i + 1]));
+    c[i] = make_float2(__uint_as_float(r[16 + 2 * i]), __uint_as_float(r[16 + 2 * i + 1]));
+  }
+}
+__device__ __forceinline__ void tmem_st8x2_nowait(uint32_t ta, uint32_t tb, const float2 (&a)[4],
+                                                  const float2 (&b)[4]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9};\n"
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%10, %11, %12, %13, %14, %15, %16, %17};\n" ::"r"(ta),
+      "r"(tb), "r"(__float_as_uint(a[0].x)), "r"(__float_as_uint(a[0].y)), "r"(__float_as_uint(a[1].x)),
+      "r"(__float_as_uint(a[1].y)), "r"(__float_as_uint(a[2].x)), "r"(__float_as_uint(a[2].y)),
+      "r"(__float_as_uint(a[3].x)), "r"(__float_as_uint(a[3].y)), "r"(__float_as_uint(b[0].x)),
+      "r"(__float_as_uint(b[0].y)), "r"(__float_as_uint(b[1].x)), "r"(__float_as_uint(b[1].y)),
+      "r"(__float_as_uint(b[2].x)), "r"(__float_as_uint(b[2].y)), "r"(__float_as_uint(b[3].x)),
+      "r"(__float_as_uint(b[3].y))
+      : "memory");
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 // Three 16-column loads of this thread's TMEM row (8 complex64 values each) under one wait.
@@ -391,7 +458,7 @@ __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (do
 // Arrival is a release reduction on a monotone counter (no round trip); the k-th barrier
 // of the launch completes when the counter reaches k * size.
 __device__ __forceinline__ bool group_barrier(Group& g, SmemRed& sm) {
-  __syncthreads();
+  wsync();
   if (threadIdx.x == 0) {
     int ok = 1;
     if (g.size > 1) {
@@ -427,7 +494,7 @@ __device__ __forceinline__ bool group_barrier(Group& g, SmemRed& sm) {
     }
     sm.flag = ok;
   }
-  __syncthreads();
+  wsync();
   return sm.flag != 0;
 }
 
@@ -438,14 +505,14 @@ __device__ __forceinline__ bool group_barrier(Group& g, SmemRed& sm) {
 // level up is float64.
 template <int NV, class A>
 __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, A (&vals)[NV], double (&out)[NV]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nwork() >> 5;
 #pragma unroll
   for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
   if (lane == 0) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) sm.warp_part[warp * kNRed + v] = (double)vals[v];
   }
-  __syncthreads();
+  wsync();
   double* slots = g.red + (size_t)(g.phase & 1) * g.stride * kNRed;
   g.phase++;
   if (warp < NV) {
@@ -467,7 +534,7 @@ __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, A (&vals)[NV
   } else if (ld_volatile_i32(g.ctrl + kCtrlAbort)) {
     return false;
   }
-  __syncthreads();
+  wsync();
 #pragma unroll
   for (int v = 0; v < NV; ++v) out[v] = sm.out[v];
   return true;
@@ -477,14 +544,14 @@ __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, A (&vals)[NV
 // partial and the sum over CTAs in float-float, one conversion to FP64 at the end.
 template <int NV>
 __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, float (&vals)[NV], double (&out)[NV]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nwork() >> 5;
 #pragma unroll
   for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
   if (lane == 0) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
   }
-  __syncthreads();
+  wsync();
   float2* slots = reinterpret_cast<float2*>(g.red + (size_t)(g.phase & 1) * g.stride * kNRed);
   g.phase++;
   if (warp < NV) {
@@ -509,7 +576,7 @@ __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, float (&vals
   } else if (ld_volatile_i32(g.ctrl + kCtrlAbort)) {
     return false;
   }
-  __syncthreads();
+  wsync();
 #pragma unroll
   for (int v = 0; v < NV; ++v) out[v] = sm.out[v];
   return true;
@@ -521,14 +588,14 @@ __device__ __forceinline__ bool group_reduce(Group& g, SmemRed& sm, float (&vals
 // warp 0 alone, sums the partials in rank order and leaves the totals in every lane.
 template <int NV>
 __device__ __forceinline__ bool reduce_ff_arrive(Group& g, SmemRed& sm, float (&vals)[NV]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nwork() >> 5;
 #pragma unroll
   for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
   if (lane == 0) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
   }
-  __syncthreads();
+  wsync();
   float2* slots = reinterpret_cast<float2*>(g.red + (size_t)(g.phase & 1) * g.stride * kNRed);
   g.phase++;  // every thread: reduce_ff_collect reads the slots of parity (phase - 1)
   if (warp < NV) {
@@ -540,7 +607,7 @@ __device__ __forceinline__ bool reduce_ff_arrive(Group& g, SmemRed& sm, float (&
     }
   }
   if (g.size > 1) return group_barrier(g, sm);
-  __syncthreads();
+  wsync();
   return ld_volatile_i32(g.ctrl + kCtrlAbort) == 0;
 }
 template <int NV>
@@ -570,7 +637,7 @@ __device__ __forceinline__ void reduce_ff_collect(Group& g, SmemRed& sm, FF (&ou
 // complex64 resident loop keeps it there rather than in every thread's stack frame): only
 // thread 0 writes it.  The barrier advances the reduction parity as well.
 __device__ __forceinline__ bool group_barrier_shared(Group& g, SmemRed& sm) {
-  __syncthreads();  // every thread has read g.phase
+  wsync();  // every thread has read g.phase
   if (threadIdx.x == 0) {
     int ok = 1;
     g.phase++;
@@ -600,19 +667,19 @@ __device__ __forceinline__ bool group_barrier_shared(Group& g, SmemRed& sm) {
     }
     sm.flag = ok;
   }
-  __syncthreads();
+  wsync();
   return sm.flag != 0;
 }
 template <int NV>
 __device__ __forceinline__ bool reduce_ff_arrive_shared(Group& g, SmemRed& sm, float (&vals)[NV]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nwork() >> 5;
 #pragma unroll
   for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
   if (lane == 0) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
   }
-  __syncthreads();
+  wsync();
   const int size = g.size;
   if (warp < NV) {
     FF s{(lane < nw) ? sm.warp_part_f[lane * kNRed + warp] : 0.f, 0.f};
@@ -627,7 +694,7 @@ __device__ __forceinline__ bool reduce_ff_arrive_shared(Group& g, SmemRed& sm, f
     }
   }
   if (size > 1) return group_barrier_shared(g, sm);
-  __syncthreads();
+  wsync();
   return ld_volatile_i32(g.ctrl + kCtrlAbort) == 0;
 }
 
@@ -658,174 +725,80 @@ __device__ __forceinline__ FF fix_to_ff(long long q, float inv_scale) {
   return {h * inv_scale, l * inv_scale};
 }
 
-// Group barrier of a Group in shared memory that also counts a fixed-point reduction.
-__device__ __forceinline__ bool group_barrier_fix(Group& g, SmemRed& sm) {
-  __syncthreads();  // every thread has read g.iseq; every partial of this CTA has been added
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    g.iseq++;
-    if (g.skip_arrival) {
-      g.skip_arrival = 0;
-    } else {
-      red_release_add_u64(g.bar, 1ull);
-    }
-    g.epoch++;
-    const unsigned long long goal = g.epoch * (unsigned long long)g.size;
-    unsigned long long t0 = 0;
-    unsigned polls = 0;
-    while (ld_acquire_u64(g.bar) < goal) {
-      if ((++polls & 31u) == 0u) {
-        if (ld_volatile_i32(g.ctrl + kCtrlAbort)) { ok = 0; break; }
-        const unsigned long long now = globaltimer_ns();
-        if (t0 == 0) {
-          t0 = now;
-        } else if ((long long)(now - t0) > g.wait_limit_ns) {
-          atomicCAS(g.ctrl + kCtrlStatus, 0, (int)KG_ERR_TIMEOUT);
-          atomicExch(g.ctrl + kCtrlAbort, 1);
-          ok = 0;
-          break;
-        }
-        if (polls > 4096u) __nanosleep(64);
-      }
-    }
-    sm.flag = ok;
-  }
-  __syncthreads();
-  return sm.flag != 0;
-}
-
-// Group sums of NV (<= 3) per-thread float values: warp sums in float, the CTA partial in
-// float-float, the group total in fixed point (scale = 2^S).  Single-CTA groups keep the CTA's
-// float-float partials in sm.cta_ff instead.  Returns false if the group aborted.
+// The control warp's side of a fixed-point group sum (one warp serves the block; the workers have
+// left their warp partials in sm.warp_part_f).  ctl_add_partials: the CTA partials in
+// float-float over the first nw warps' entries, added as fixed-point numbers into the ring slot
+// of reduction g.iseq (lane 0; single-CTA groups keep the float-float values in sm.cta_ff).
 template <int NV>
-__device__ __forceinline__ bool reduce_fix_arrive_shared(Group& g, SmemRed& sm, float (&vals)[NV], float scale) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ __forceinline__ void ctl_add_partials(const Group& g, SmemRed& sm, int nw, float scale) {
+  const int lane = threadIdx.x & 31;
+  FF s[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
-  if (lane == 0) {
+  for (int v = 0; v < NV; ++v) s[v] = FF{(lane < nw) ? sm.warp_part_f[lane * kNRed + v] : 0.f, 0.f};
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
+  for (int v = 0; v < NV; ++v) s[v] = ff_warp_sum(s[v]);
+  if (lane != 0) return;
+  if (g.size == 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm.cta_ff[v] = make_float2(s[v].hi, s[v].lo);
+    return;
   }
-  __syncthreads();
-  const int size = g.size;
   const unsigned slot = g.iseq % (unsigned)kIRing;
-  if (warp < NV) {
-    FF s{(lane < nw) ? sm.warp_part_f[lane * kNRed + warp] : 0.f, 0.f};
-    s = ff_warp_sum(s);
-    if (lane == 0) {
-      if (size > 1) {
-        unsigned bad = 0u;
-        const long long q = ff_to_fix(s, scale, bad);
-        unsigned long long* r = g.iring + 4u * slot;
-        red_relaxed_add_u64(r + warp, (unsigned long long)q);
-        if (bad) red_relaxed_add_u64(r + 3, 1ull);
-      } else {
-        sm.cta_ff[warp] = make_float2(s.hi, s.lo);
-      }
-    }
-  }
-  if (size > 1) {
-    if (threadIdx.x == 32 * NV && g.rank == 0) {
-      unsigned long long* z = g.iring + 4u * ((slot + 2u) % (unsigned)kIRing);
-      __stcg(z, 0ull);
-      __stcg(z + 1, 0ull);
-      __stcg(z + 2, 0ull);
-      __stcg(z + 3, 0ull);
-    }
-    return group_barrier_fix(g, sm);
-  }
-  __syncthreads();
-  return ld_volatile_i32(g.ctrl + kCtrlAbort) == 0;
-}
-
-// The same reduction split at its barrier: reduce_fix_arrive adds this CTA's partials and
-// arrives (nothing waits), so that the CTA can do work of its own -- which must not read what
-// other CTAs write before this barrier -- until group_wait_fix waits for every other arrival.
-template <int NV>
-__device__ __forceinline__ void reduce_fix_arrive(Group& g, SmemRed& sm, float (&vals)[NV], float scale) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long* r = g.iring + 4u * slot;
+  unsigned bad = 0u;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) vals[v] = warp_sum(vals[v]);
-  if (lane == 0) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sm.warp_part_f[warp * kNRed + v] = vals[v];
-  }
-  __syncthreads();
-  const int size = g.size;
-  const unsigned slot = g.iseq % (unsigned)kIRing;
-  if (warp < NV) {
-    FF s{(lane < nw) ? sm.warp_part_f[lane * kNRed + warp] : 0.f, 0.f};
-    s = ff_warp_sum(s);
-    if (lane == 0) {
-      if (size > 1) {
-        unsigned bad = 0u;
-        const long long q = ff_to_fix(s, scale, bad);
-        unsigned long long* r = g.iring + 4u * slot;
-        red_relaxed_add_u64(r + warp, (unsigned long long)q);
-        if (bad) red_relaxed_add_u64(r + 3, 1ull);
-      } else {
-        sm.cta_ff[warp] = make_float2(s.hi, s.lo);
-      }
-    }
-  }
-  if (size > 1 && threadIdx.x == 32 * NV && g.rank == 0) {
+  for (int v = 0; v < NV; ++v) red_relaxed_add_u64(r + v, (unsigned long long)ff_to_fix(s[v], scale, bad));
+  if (bad) red_relaxed_add_u64(r + 3, 1ull);
+  if (g.rank == 0) {
     unsigned long long* z = g.iring + 4u * ((slot + 2u) % (unsigned)kIRing);
     __stcg(z, 0ull);
     __stcg(z + 1, 0ull);
     __stcg(z + 2, 0ull);
     __stcg(z + 3, 0ull);
   }
-  __syncthreads();  // every thread has read g.iseq; every partial of this CTA has been added
-  if (threadIdx.x == 0) {
-    g.iseq++;
-    if (size > 1) {
-      if (g.skip_arrival) {  // injected fault: this CTA never joins; its own wait runs out too
-        g.skip_arrival = 0;
-      } else {
-        red_release_add_u64(g.bar, 1ull);
-      }
-      g.epoch++;
+}
+// Lane 0 of the control warp: the CTA's arrival at the group barrier that closes reduction
+// g.iseq.  The release orders every store of the block before it (the workers handed over at a
+// named barrier), so it waits for the block's stores to drain; no worker waits with it.
+__device__ __forceinline__ void ctl_arrive(Group& g) {
+  g.iseq++;
+  if (g.size > 1) {
+    if (g.skip_arrival) {  // injected fault: this CTA never joins; its own wait runs out too
+      g.skip_arrival = 0;
+    } else {
+      red_release_add_u64(g.bar, 1ull);
     }
+    g.epoch++;
   }
 }
-// Every thread: wait for the barrier reduce_fix_arrive arrived at (bounded, as group_barrier);
-// false if the group aborted or the wait ran out.
-__device__ __forceinline__ bool group_wait_fix(Group& g, SmemRed& sm) {
-  __syncthreads();  // thread 0 has arrived; every thread has read g
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    if (g.size > 1) {
-      const unsigned long long goal = g.epoch * (unsigned long long)g.size;
-      unsigned long long t0 = 0;
-      unsigned polls = 0;
-      while (ld_acquire_u64(g.bar) < goal) {
-        if ((++polls & 31u) == 0u) {
-          if (ld_volatile_i32(g.ctrl + kCtrlAbort)) { ok = 0; break; }
-          const unsigned long long now = globaltimer_ns();
-          if (t0 == 0) {
-            t0 = now;
-          } else if ((long long)(now - t0) > g.wait_limit_ns) {
-            atomicCAS(g.ctrl + kCtrlStatus, 0, (int)KG_ERR_TIMEOUT);
-            atomicExch(g.ctrl + kCtrlAbort, 1);
-            ok = 0;
-            break;
-          }
-          if (polls > 4096u) __nanosleep(64);
-        }
+// Lane 0 of the control warp: wait for every arrival at the last barrier (bounded, as
+// group_barrier); false if the group aborted or the wait ran out.
+__device__ __forceinline__ bool ctl_wait(const Group& g) {
+  if (g.size == 1) return ld_volatile_i32(g.ctrl + kCtrlAbort) == 0;
+  const unsigned long long goal = g.epoch * (unsigned long long)g.size;
+  unsigned long long t0 = 0;
+  unsigned polls = 0;
+  while (ld_acquire_u64(g.bar) < goal) {
+    if ((++polls & 31u) == 0u) {
+      if (ld_volatile_i32(g.ctrl + kCtrlAbort)) return false;
+      const unsigned long long now = globaltimer_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if ((long long)(now - t0) > g.wait_limit_ns) {
+        atomicCAS(g.ctrl + kCtrlStatus, 0, (int)KG_ERR_TIMEOUT);
+        atomicExch(g.ctrl + kCtrlAbort, 1);
+        return false;
       }
-    } else if (ld_volatile_i32(g.ctrl + kCtrlAbort)) {
-      ok = 0;
+      if (polls > 4096u) __nanosleep(64);
     }
-    sm.flag = ok;
   }
-  __syncthreads();
-  return sm.flag != 0;
+  return true;
 }
 
-// Totals of the group's last fixed-point reduction (thread 0, after its barrier), in two parts
-// so that the L2 load can be issued early and its result used late: fix_load reads the slot's
-// four words, fix_totals turns them into float-float values (false if a partial was out of
-// range).  Single-CTA groups: the CTA's own partials.
+// Totals of the group's last fixed-point reduction (lane 0 of the control warp, after its
+// barrier), in two parts: fix_load reads the slot's four words, fix_totals turns them into
+// float-float values (false if a partial was out of range).  Single-CTA groups: the CTA's own
+// partials.
 struct FixRaw {
   unsigned long long w[4];
 };
@@ -837,13 +810,6 @@ __device__ __forceinline__ FixRaw fix_load(const Group& g) {
     for (int v = 0; v < 4; ++v) r.w[v] = __ldcg(s + v);  // weak: the barrier's acquire ordered it
   }
   return r;
-}
-// The same four words copied into shared memory by an asynchronous copy (cp.async, two 16-byte
-// pieces; the caller commits and waits), so that no register holds them meanwhile.
-__device__ __forceinline__ void fix_load_async(const Group& g, FixRaw* dst) {
-  const unsigned long long* s = g.iring + 4u * ((g.iseq - 1u) % (unsigned)kIRing);
-  cp_async16(&dst->w[0], s);
-  cp_async16(&dst->w[2], s + 2);
 }
 template <int NV>
 __device__ __forceinline__ bool fix_totals(const Group& g, const SmemRed& sm, const FixRaw& r, float inv_scale,

@@ -48,6 +48,15 @@ constexpr int kStrSvBufs = 2;  // tiles of v_k for the stencil (1: one more barr
 constexpr size_t kStrSmemBytes = (size_t)kStrSvBufs * 4096 * 8 + (size_t)kStrDepth * 4 * 512 * 16;    // Lanczos partner ring: 4 x 32 KB behind the 64 KB of v_k
 constexpr int kLzMaxChunks = 2 * (1 + (kMaxL - 13) + 1);  // two tiles: bond 11, outer bonds, Sx site
 constexpr uint32_t kTmemCols = 512;  // 128 columns per warp, 4 warps per lane quarter
+// Headline loop (lanczos_res64b): 16 worker warps and the control warp (warp 16), which meet at
+// named barriers -- kBarPost (workers arrive with a step's partial sums, the control warp waits),
+// kBarGroup (the control warp arrives once the group barrier has passed) and kBarScal (it
+// arrives once the next step's scalars are formed).  Barrier 1 is the workers' own (wsync).
+constexpr int kCtlThreads = kThreads + 32;
+enum { kBarPost = 2, kBarGroup = 3, kBarScal = 4 };
+constexpr int kCtlLast = 1 << 16;  // ctl_cmd flag: the slice's last step
+constexpr int kCtlExit = -1;       // ctl_cmd: the evaluation is over
+static_assert(kThreads == kWorkMax, "worker threads of a block");
 
 // What the complex64 resident loop reads in its steps, per CTA (shared memory).
 struct ResCtx {
@@ -89,7 +98,8 @@ struct SmemSlice {
   Group grp;  // the group's barrier state while the resident loop runs (written by thread 0)
   float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
   float4 slotbuf[2 * kSlotRanks];  // the group's reduction slots, prefetched by warp 0
-  FixRaw fixraw;                   // the fixed-point totals of the last step (lanczos_res64b)
+  int ctl_cmd;  // control warp: the step whose sums were handed over (| kCtlLast), or kCtlExit
+  int ctl_ok;   // control warp: the group barrier passed (0: aborted or timed out)
   unsigned ff_e_set;
   uint32_t tmem_base;
 };
@@ -383,7 +393,7 @@ __device__ __noinline__ bool reorth_cgs2(Ctx<V>& c, int k, const V* src, V* r_g)
         }
       }
     }
-    __syncthreads();
+    wsync();
     for (int ct = 0; ct < c.n_own; ++ct) {
       const size_t base = c.tile_base(ct);
 #pragma unroll
@@ -435,7 +445,7 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
   V X[RES ? 1 : NB][RES ? 1 : APT];  // streaming: part of H v_k leaving the tile (resident: in c.sx)
   double amax = 0.0, bmax = 0.0;     // thread 0: running maxima for the breakdown test
   if (tid == 0) lz_init(ss, nrm_src, m);
-  __syncthreads();
+  wsync();
   if (ss.meff > 0) {
     for (int k = 0; k < m; ++k) {
       const bool last = (k == m - 1);
@@ -511,7 +521,7 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
             }
           }
         }
-        __syncthreads();
+        wsync();
         c.mark(0);
         // ---- stage 2: H v_k, W_{k+1} = H v_k - b_k v_{k-1}, partial sums
 #pragma unroll
@@ -553,14 +563,14 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
             if constexpr (!RES) stv((V*)p.xbuf + base + li, X[0][j]);
           }
         }
-        if (!RES) __syncthreads();
+        if (!RES) wsync();
       }
       c.mark(1);
       double out[3];
       if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
       c.mark(2);
       if (tid == 0) lz_after_reduce(ss, k, last, out);
-      __syncthreads();
+      wsync();
       const int code = ss.code1;
       if (code == 2) {
         if (tid == 0) flag_nonfinite(p);
@@ -600,7 +610,7 @@ __device__ __forceinline__ bool lanczos_generic(Ctx<V>& c, const V* src, double 
           ss.f_ap = 0.f;
         }
       }
-      __syncthreads();
+      wsync();
       c.mark(3);
       if (ss.stop) break;
     }
@@ -728,7 +738,7 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
   if constexpr (WBASIS) {
     rb[0] = (c.n_own > 0) ? c.tile_base(0) : 0;
     rb[1] = (c.n_own > 1) ? c.tile_base(1) : 0;
-    __syncthreads();  // every thread is done with the Lanczos loop's shared memory
+    wsync();  // every thread is done with the Lanczos loop's shared memory
     if (tid >= 32) {  // warp 0 issues its copies after the exponential
       for (int s = 0; s < kRecombDepth; ++s) {
         if (s < meff) {  // newest basis vector first (see the loop below)
@@ -801,7 +811,7 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
       }
     }
   }
-  __syncthreads();
+  wsync();
   c.mark(4);
   if (tid == 0 && meff > 0 && !interior) c.breakdowns += ss.broke ? 1 : 0;
   // ---- recombination dst = sum_k coef_k (basis slot k) (+ fused norms / overlaps)
@@ -920,7 +930,7 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
     ss.nrm_out = sqrt(fmax(out[0], 0.0));
     ss.code1 = isfinite(out[0]) ? 0 : 2;
   }
-  __syncthreads();
+  wsync();
   if (ss.code1 == 2) {
     if (tid == 0) flag_nonfinite(p);
     return false;
@@ -1231,7 +1241,7 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
       for (int j = 0; j < APT; ++j) sw[cc * T + tid + j * NT] = ldv(src + base + tid + j * NT);
     }
   }
-  __syncthreads();
+  wsync();
   if (ss.meff == 0) return true;
   const int m = ss.r.m;
   unsigned gbase = c.lz_count;  // running number of the step's first ring copy
@@ -1277,7 +1287,7 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
           }
           // Every thread is done with stage st: its reads have returned, so the next copy may
           // overwrite it (no proxy fence: a fence here would wait for the copies in flight).
-          if (__syncthreads_or(!ok)) return false;
+          if (wsync_or(!ok)) return false;
           if (tid == 0 && r + kLzStages < nB) lz_issue(ss, vec, iB0 + r + kLzStages, g + kLzStages);
         }
       }
@@ -1328,7 +1338,7 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
         tmem_st8c(tP, hw);
       }
       if (qq == 0 && k > 0 && tid < 32) warp0_scalars(ss, k - 1, false);
-      __syncthreads();  // the scalars of step k; every neighbour read of W_k in this tile done
+      wsync();  // the scalars of step k; every neighbour read of W_k in this tile done
       if (qq == 0 && k > 0) {
         const int code = ss.code1;
         if (code == 2) {
@@ -1361,10 +1371,10 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
               lzf_finish_step(ss, k - 1, false, o1[0], ss.r.bdtol, ss.r.amax, ss.r.bmax);
             }
           }
-          __syncthreads();
+          wsync();
         }
         if (ss.stop) {  // breakdown: v_k does not exist; the copies started for step k are not used
-          if (__syncthreads_or(!ring_drain(p, ss, gbase))) return false;
+          if (wsync_or(!ring_drain(p, ss, gbase))) return false;
           gbase += (unsigned)min(ring_n(ss), kLzStages);
           stopped = true;
           break;
@@ -1433,7 +1443,7 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
       slot_prefetch(ss);  // (the last step did not prefetch)
       warp0_scalars(ss, m - 1, true);
     }
-    __syncthreads();
+    wsync();
     if (ss.code1 == 2) {
       if (tid == 0) flag_nonfinite(p);
       return false;
@@ -1617,7 +1627,7 @@ __device__ __noinline__ bool res64b_explicit_norm(SmemSlice& ss, uint32_t tV, in
       lzf_finish_step(ss, k - 1, false, o1[0], ss.r.bdtol, ss.r.amax, ss.r.bmax);
     }
   }
-  __syncthreads();
+  wsync();
   return true;
 }
 
@@ -1626,18 +1636,22 @@ __device__ __noinline__ bool res64b_explicit_norm(SmemSlice& ss, uint32_t tV, in
 // recurrence, basis slots holding W_k, v_{k-1} and H v_{k-1} in tensor memory, W_k of the own
 // tiles in shared memory), in the pair layout -- thread tid owns the amplitude pairs
 // P = tid + 512 g (g < 4) of each own tile, amplitudes 2P and 2P + 1, so that every vector access
-// moves 16 bytes -- with the group barrier split in two and group sums in fixed point.  Step k:
-//   1. (W_k is visible to the group; the in-tile part of H W_k is parked in tensor memory)
-//      thread 0 starts an asynchronous copy of the previous step's totals;
+// moves 16 bytes -- with group sums in fixed point, served by the block's control warp
+// (res64b_control).  Step k, for the 16 worker warps:
+//   1. (the in-tile part of H W_k is parked in tensor memory) wait until W_k is visible to the
+//      group (named barrier kBarGroup; nothing to wait for at k = 0);
 //   2. both tiles: H W_k = the parked in-tile part + the partner blocks of W_k from other tiles
 //      (plain L2 loads, two table entries in flight);
-//   3. thread 0 forms alpha_{k-1}, b_k (float-float) and the scalars of step k; block barrier;
+//   3. take alpha_{k-1}, b_k and the scalars of step k, which the control warp formed from the
+//      group totals during stage 2 (named barrier kBarScal); b_k explicitly near an invariant
+//      subspace;
 //   4. both tiles: v_k, H v_k, W_{k+1} (shared memory and basis slot k+1), partial sums;
-//   5. CTA partials in float-float, fixed-point group sums, arrival at the group barrier;
-//   6. while the other CTAs arrive: the in-tile part of H W_{k+1} (shared memory only; the
-//      diagonal was formed once per slice), parked in tensor memory;
-//   7. wait for the group barrier.
-// Stage 6 covers the barrier's latency and the draining of the W_{k+1} stores.  Tensor-memory
+//   5. hand the warps' partial sums to the control warp (named barrier kBarPost; no wait): it
+//      adds the CTA's share to the group sums and arrives at the group barrier, which waits
+//      for the W_{k+1} stores to drain;
+//   6. meanwhile, after a workers' barrier: the in-tile part of H W_{k+1} (shared memory only;
+//      the diagonal was formed once per slice), parked in tensor memory.
+// No worker waits for a store to drain, polls the group barrier or forms a scalar.  Tensor-memory
 // stores are not waited for where they are issued; one wait comes before the next loads.
 __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, double nrm_src, double uj) {
   const EvalParams& p = *c.p;
@@ -1714,21 +1728,25 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
       }
     }
   }
-  __syncthreads();
+  wsync();
   if (ss.meff == 0) return true;
   const int m = ss.r.m;
   const int n_own = ss.r.n_own;
   for (int cc = 0; cc < n_own; ++cc) stencil_park(ss, cc, tP);  // in-tile part of H W_0
   const float2* vec = src;  // W_k: the vector whose partner blocks are read in step k
   bool done = false;
-  bool redo = false;  // the step is run again after its b_k was formed explicitly
   for (int k = 0; k < m; ++k) {
     const bool last = (k == m - 1);
     float2* wdst = last ? nullptr : ss.r.basis + (size_t)k * ss.r.D;  // W_{k+1}: basis slot k+1
-    // ---- 1. the previous step's totals (thread 0; the copy's latency passes under stage 2)
-    if (tid == 0 && k > 0 && !redo && ss.grp.size > 1) {
-      fix_load_async(ss.grp, &ss.fixraw);
-      cp_async_commit();
+    // ---- 1. W_k is visible to the group (the barrier of step k - 1)
+    if (k > 0) {
+      nbar_sync(kBarGroup, kCtlThreads);
+      if (!ss.ctl_ok) {
+        nbar_sync(kBarScal, kCtlThreads);
+        tmem_st_wait();
+        return false;
+      }
+      if (prof) prof_mark(ss, 2);
     }
     // ---- 2. H W_k of both tiles: the parked in-tile part plus the partner blocks, parked again
     tmem_st_wait();
@@ -1740,36 +1758,21 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
       tmem_st8c_nowait(tP + 16u * cc, h);
     }
     if (prof) prof_mark(ss, 0);
-    // ---- 3. alpha_{k-1}, b_k and the scalars of step k (thread 0), one block barrier
-    if (tid == 0 && k > 0 && !redo) {
-      FF tot[3];
-      if (ss.grp.size > 1) cp_async_wait<0>();
-      if (!fix_totals<3>(ss.grp, ss.red, ss.fixraw, ss.r.finv, tot)) {
-        ss.code1 = 2;
-      } else {
-        const FF b2 = lzf_after_reduce(ss, k - 1, false, tot);
-        if (ss.code1 == 0) lzf_finish_step(ss, k - 1, false, b2, ss.r.bdtol, ss.r.amax, ss.r.bmax);
-      }
-    }
-    __syncthreads();  // the scalars of step k
-    if (k > 0 && !redo) {
+    // ---- 3. alpha_{k-1}, b_k and the scalars of step k (formed by the control warp)
+    if (k > 0) {
+      nbar_sync(kBarScal, kCtlThreads);
       const int code = ss.code1;
       if (code == 2) {
         tmem_st_wait();
         if (tid == 0) flag_nonfinite(p);
         return false;
       }
-      if (code == 1) {  // near an invariant subspace: form b_k explicitly, then run step k again
+      if (code == 1) {  // near an invariant subspace: b_k from ||W_k - alpha_{k-1} v_{k-1}||^2
         tmem_st_wait();
         if (!res64b_explicit_norm(ss, tV, k)) return false;
-        if (ss.stop) break;
-        redo = true;
-        --k;
-        continue;
       }
       if (ss.stop) break;  // breakdown: v_k does not exist
     }
-    redo = false;
     if (prof) prof_mark(ss, 3);
     // ---- 4. v_k, H v_k, W_{k+1} = H v_k - b_k v_{k-1} for the own amplitudes; partial sums
     float2 acc_a = f2(0.f), acc_n = f2(0.f), acc_q = f2(0.f);
@@ -1779,74 +1782,76 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
 #pragma unroll 1
       for (int cc = 0; cc < n_own; ++cc) {
         float4* sw4 = reinterpret_cast<float4*>(ss.r.sw + cc * T);
-        float2 vp[8], hp[8], wo[8], hw[8];
-        tmem_ld8c_x3(tP + 16u * cc, tV + 16u * cc, tH + 16u * cc, hw, vp, hp);  // vp, hp unused at k = 0
+        float4* d4 = last ? nullptr : reinterpret_cast<float4*>(wdst + ss.r.tbase[cc]);
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const float4 w4 = sw4[tid + 512 * g];
-          wo[2 * g] = lo2(w4);
-          wo[2 * g + 1] = hi2(w4);
-        }
+        for (int hf = 0; hf < 2; ++hf) {  // pairs g = 2 hf, 2 hf + 1: TMEM columns 8 hf .. 8 hf + 7
+          const uint32_t co = 16u * cc + 8u * hf;
+          float2 vp[4], hp[4], wo[4], hw[4];
+          tmem_ld4c_x3(tP + co, tV + co, tH + co, hw, vp, hp);  // vp, hp unused at k = 0
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          float2 v, hv, w;
-          if (k == 0) {
-            v = f2mul(wo[a], f2(ib));
-            hv = f2mul(hw[a], f2(ib));
-            w = hv;
-          } else {
-            v = f2mul(f2fma(f2(-ap), vp[a], wo[a]), f2(ib));
-            hv = f2mul(f2fma(f2(-ap), hp[a], hw[a]), f2(ib));
-            w = f2fma(f2(-bk), vp[a], hv);
+          for (int x = 0; x < 2; ++x) {
+            const float4 w4 = sw4[tid + 512 * (2 * hf + x)];
+            wo[2 * x] = lo2(w4);
+            wo[2 * x + 1] = hi2(w4);
           }
-          acc_a = f2fma(v, w, acc_a);
-          acc_n = f2fma(w, w, acc_n);
-          acc_q = f2fma(v, v, acc_q);
-          vp[a] = v;
-          hp[a] = hv;
-          wo[a] = w;
-        }
-        if (!last) {
-          tmem_st16x2_nowait(tV + 16u * cc, tH + 16u * cc, vp, hp);
-          float4* d4 = reinterpret_cast<float4*>(wdst + ss.r.tbase[cc]);
-          const unsigned long long keep = l2_evict_last();
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const float4 w4 = pair4(wo[2 * g], wo[2 * g + 1]);
-            sw4[tid + 512 * g] = w4;
-            stv4_hint(d4 + tid + 512 * g, w4, keep);
+          for (int a = 0; a < 4; ++a) {
+            float2 v, hv, w;
+            if (k == 0) {
+              v = f2mul(wo[a], f2(ib));
+              hv = f2mul(hw[a], f2(ib));
+              w = hv;
+            } else {
+              v = f2mul(f2fma(f2(-ap), vp[a], wo[a]), f2(ib));
+              hv = f2mul(f2fma(f2(-ap), hp[a], hw[a]), f2(ib));
+              w = f2fma(f2(-bk), vp[a], hv);
+            }
+            acc_a = f2fma(v, w, acc_a);
+            acc_n = f2fma(w, w, acc_n);
+            acc_q = f2fma(v, v, acc_q);
+            vp[a] = v;
+            hp[a] = hv;
+            wo[a] = w;
+          }
+          if (!last) {
+            tmem_st8x2_nowait(tV + co, tH + co, vp, hp);
+            const unsigned long long keep = l2_evict_last();
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+              const int g = 2 * hf + x;
+              const float4 w4 = pair4(wo[2 * x], wo[2 * x + 1]);
+              sw4[tid + 512 * g] = w4;
+              stv4_hint(d4 + tid + 512 * g, w4, keep);
+            }
           }
         }
       }
     }
     if (prof) prof_mark(ss, 1);
-    // ---- 5. group sums of step k; arrival
-    float acc[3] = {acc_a.x + acc_a.y, acc_n.x + acc_n.y, acc_q.x + acc_q.y};
-    reduce_fix_arrive<3>(ss.grp, ss.red, acc, ss.r.fscale);
-    // ---- 6. the in-tile part of H W_{k+1} while the group arrives
-    if (!last)
-      for (int cc = 0; cc < n_own; ++cc) stencil_park(ss, cc, tP);
-    // ---- 7. the group barrier
-    if (!group_wait_fix(ss.grp, ss.red)) {
-      tmem_st_wait();
-      return false;
+    // ---- 5. the warps' partial sums of step k to the control warp (it arrives for the CTA)
+    {
+      float acc[3] = {warp_sum(acc_a.x + acc_a.y), warp_sum(acc_n.x + acc_n.y), warp_sum(acc_q.x + acc_q.y)};
+      if ((tid & 31) == 0) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) ss.red.warp_part_f[(tid >> 5) * kNRed + v] = acc[v];
+      }
+      if (tid == 0) ss.ctl_cmd = k | (last ? kCtlLast : 0);
+      nbar_arrive(kBarPost, kCtlThreads);
     }
-    if (prof) prof_mark(ss, 2);
+    // ---- 6. the in-tile part of H W_{k+1} while the group arrives (it reads other threads'
+    // amplitudes of W_{k+1} in shared memory: one workers' barrier first)
+    if (!last) {
+      wsync();
+      for (int cc = 0; cc < n_own; ++cc) stencil_park(ss, cc, tP);
+    }
     vec = wdst;
     if (last) done = true;
   }
   tmem_st_wait();  // every store of v_k, H v_k has completed
-  if (done) {  // the sums of the last step: alpha_{m-1}, b_m (error indicator)
-    if (tid == 0) {
-      FF tot[3];
-      if (!fix_totals<3>(ss.grp, ss.red, fix_load(ss.grp), ss.r.finv, tot)) {
-        ss.code1 = 2;
-      } else {
-        const FF b2 = lzf_after_reduce(ss, m - 1, true, tot);
-        if (ss.code1 == 0) lzf_finish_step(ss, m - 1, true, b2, ss.r.bdtol, ss.r.amax, ss.r.bmax);
-      }
-    }
-    __syncthreads();
+  if (done) {  // the last step's sums: alpha_{m-1}, b_m (error indicator), formed by the control warp
+    nbar_sync(kBarGroup, kCtlThreads);
+    nbar_sync(kBarScal, kCtlThreads);
+    if (!ss.ctl_ok) return false;
     if (ss.code1 == 2) {
       if (tid == 0) flag_nonfinite(p);
       return false;
@@ -1858,6 +1863,45 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
   c.g.iseq = ss.grp.iseq;
   if (tid < 32) lzf_build_T(ss, m);
   return true;
+}
+
+// The control warp of the headline kernel (threads kThreads .. kThreads + 31): serves the group
+// sums of lanczos_res64b until the workers send kCtlExit.  For Lanczos step k it takes the
+// workers' warp partials (kBarPost), adds the CTA's share to the group's fixed-point sums,
+// arrives at the group barrier -- the release waits for the block's W_{k+1} stores to drain --
+// and waits for the group (kBarGroup); then, while the workers read the partner blocks of
+// W_{k+1}, it reads the totals and forms alpha_k, b_{k+1} and the scalars of step k + 1
+// (kBarScal).  Every step handed over is answered at both barriers, also when the group aborts.
+__device__ __noinline__ void res64b_control(SmemSlice& ss) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    nbar_sync(kBarPost, kCtlThreads);
+    const int cmd = ss.ctl_cmd;
+    if (cmd == kCtlExit) return;
+    const int k = cmd & (kCtlLast - 1);
+    const bool last = (cmd & kCtlLast) != 0;
+    Group& g = ss.grp;
+    ctl_add_partials<3>(g, ss.red, kThreads / 32, ss.r.fscale);
+    bool ok = true;
+    if (lane == 0) {
+      ctl_arrive(g);
+      ok = ctl_wait(g);
+      ss.ctl_ok = ok ? 1 : 0;
+    }
+    __syncwarp();
+    nbar_arrive(kBarGroup, kCtlThreads);
+    if (lane == 0 && ok) {
+      FF tot[3];
+      if (!fix_totals<3>(g, ss.red, fix_load(g), ss.r.finv, tot)) {
+        ss.code1 = 2;
+      } else {
+        const FF b2 = lzf_after_reduce(ss, k, last, tot);
+        if (ss.code1 == 0) lzf_finish_step(ss, k, last, b2, ss.r.bdtol, ss.r.amax, ss.r.bmax);
+      }
+    }
+    __syncwarp();
+    nbar_arrive(kBarScal, kCtlThreads);
+  }
 }
 
 // ---------------------------------------------------------------- complex64 streaming path
@@ -2011,7 +2055,7 @@ __device__ __noinline__ bool lanczos_str64(Ctx<float2>& c, const float2* src, do
   float2* xb = (float2*)p.xbuf;
   double amax = 0.0, bmax = 0.0;  // thread 0: running maxima for the breakdown test
   if (tid == 0) lz_init(ss, nrm_src, m);
-  __syncthreads();
+  wsync();
   if (ss.meff == 0) return true;
   StrStep S;
   S.L1 = L1;
@@ -2071,7 +2115,7 @@ __device__ __noinline__ bool lanczos_str64(Ctx<float2>& c, const float2* src, do
 #pragma unroll
         for (int g = 0; g < 4; ++g) x[g] = f4scale(ib, xs[g]);
       }
-      if (kStrSvBufs == 1) __syncthreads();  // the previous tile's stencil is done with sv
+      if (kStrSvBufs == 1) wsync();  // the previous tile's stencil is done with sv
       {
         const float4* q = str_wait(ring, cslot);
 #pragma unroll
@@ -2092,7 +2136,7 @@ __device__ __noinline__ bool lanczos_str64(Ctx<float2>& c, const float2* src, do
         str_issue_next(c, S, iu, ring, islot);
         cslot = (cslot + 1 == kStrDepth) ? 0 : cslot + 1;
       }
-      __syncthreads();  // the tile's v_k is complete in shared memory
+      wsync();  // the tile's v_k is complete in shared memory
       float4 vv[4];
 #pragma unroll
       for (int g = 0; g < 4; ++g) vv[g] = sv[tid + g * NT];
@@ -2166,7 +2210,7 @@ __device__ __noinline__ bool lanczos_str64(Ctx<float2>& c, const float2* src, do
     if (!group_reduce<3>(c.g, ss.red, acc, out)) return false;
     c.mark(2);
     if (tid == 0) lz_after_reduce(ss, k, last, out);
-    __syncthreads();
+    wsync();
     const int code = ss.code1;
     if (code == 2) {
       if (tid == 0) flag_nonfinite(p);
@@ -2193,7 +2237,7 @@ __device__ __noinline__ bool lanczos_str64(Ctx<float2>& c, const float2* src, do
       if (tid == 0) ss.s_b2 = o1[0];
     }
     if (tid == 0) lz_finish_step(ss, k, last, p.bd_tol, amax, bmax);
-    __syncthreads();
+    wsync();
     c.mark(3);
     if (ss.stop) break;
   }
@@ -2234,7 +2278,7 @@ __device__ bool init_costate(Ctx<V>& c, double2 beta, V* chi, const V* psiN, dou
   double acc[2] = {0.0, 0.0};
   for (int ct = 0; ct < c.n_own; ++ct) {
     const size_t base = c.tile_base(ct);
-    for (int li = threadIdx.x; li < c.tile; li += blockDim.x) {
+    for (int li = threadIdx.x; li < c.tile; li += nwork()) {
       const size_t gi = base + li;
       const double2 f = reinterpret_cast<const double2*>(p.target)[gi];
       const double yr = beta.x * f.x - beta.y * f.y, yi = beta.x * f.y + beta.y * f.x;
@@ -2271,7 +2315,7 @@ __device__ bool init_state(Ctx<V>& c, V* dst, double& nrm) {
   double acc[1] = {0.0};
   for (int ct = 0; ct < c.n_own; ++ct) {
     const size_t base = c.tile_base(ct);
-    for (int li = threadIdx.x; li < c.tile; li += blockDim.x) {
+    for (int li = threadIdx.x; li < c.tile; li += nwork()) {
       const size_t gi = base + li;
       const double2 a = reinterpret_cast<const double2*>(p.psi0)[gi];
       const V y = vmake<V>((R)a.x, (R)a.y);
@@ -2447,9 +2491,9 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
   }
   // ---- outputs (rank 0)
   if (rank == 0) {
-    __syncthreads();
+    wsync();
     if (p.grad_mode != KG_GRAD_NONE) {
-      for (int j = threadIdx.x; j < p.N; j += blockDim.x) {
+      for (int j = threadIdx.x; j < p.N; j += nwork()) {
         const double gl = p.G[j], gr = p.G[j + 1];
         if (p.grad_mode == KG_GRAD_EXACT)  // Gauss-Lobatto weights 1/12, 5/12, 5/12, 1/12
           p.grad[j] = (gl + gr) / 12.0 + 5.0 * (p.Gi[2 * j] + p.Gi[2 * j + 1]) / 12.0;
@@ -2494,14 +2538,27 @@ __device__ __forceinline__ void cta_teardown(SmemSlice& ss, bool tmem) {
   if (threadIdx.x < 32) tmem_dealloc(ss.tmem_base, kTmemCols);
 }
 
+// Threads per CTA of an evaluation kernel: the headline loop's blocks carry the control warp.
+constexpr int eval_threads(int mode) { return mode == kModeResident64b ? kCtlThreads : kThreads; }
+
 template <class V, class A, int APT, int TPC, bool RES, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) kg_eval_kernel(const __grid_constant__ EvalParams p) {
+__global__ void __launch_bounds__(eval_threads(MODE), 1) kg_eval_kernel(const __grid_constant__ EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ SmemSlice ss;
   constexpr bool kTmem = (MODE == kModeResident64 || MODE == kModeResident64b);
   cta_setup(ss, kTmem);
   unsigned lz_count = 0u;  // Lanczos ring copies consumed (stage and phase parity of the ring)
-  run_eval<V, A, APT, TPC, RES, MODE>(p, blockIdx.x, gridDim.x, ss, smem_dyn, lz_count);
+  if constexpr (MODE == kModeResident64b) {
+    if (threadIdx.x >= kThreads) {
+      res64b_control(ss);
+    } else {
+      run_eval<V, A, APT, TPC, RES, MODE>(p, blockIdx.x, gridDim.x, ss, smem_dyn, lz_count);
+      if (threadIdx.x == 0) ss.ctl_cmd = kCtlExit;  // no step is in flight: every one was answered
+      nbar_arrive(kBarPost, kCtlThreads);
+    }
+  } else {
+    run_eval<V, A, APT, TPC, RES, MODE>(p, blockIdx.x, gridDim.x, ss, smem_dyn, lz_count);
+  }
   cta_teardown(ss, kTmem);
 }
 
@@ -2531,7 +2588,7 @@ __global__ void __launch_bounds__(kThreads, 1) kg_batch_kernel(const __grid_cons
     else
       ok = run_eval<float2, float, 8, 1, false, kModeGeneric>(p, item.rank, item.size, ss, smem_dyn, lz_count);
     if (!ok) break;
-    __syncthreads();
+    wsync();
   }
   cta_teardown(ss, true);
 }
@@ -2573,6 +2630,7 @@ cudaError_t batch_kernel_max_ctas(int* out) {
 struct KernelChoice {
   const void* fn;
   size_t smem;
+  int threads;
 };
 
 template <class V, class A, int APT, int TPC, bool RES, int MODE>
@@ -2581,7 +2639,7 @@ static KernelChoice choice(int t_bits) {
   // complex64 streaming: two v_k tiles for the stencil plus the per-thread copy ring
   const size_t smem = (MODE == kModeStream64) ? kStrSmemBytes
                                               : (size_t)(RES ? 3 : 2) * NB * ((size_t)1 << t_bits) * sizeof(V);
-  return {(const void*)kg_eval_kernel<V, A, APT, TPC, RES, MODE>, smem};
+  return {(const void*)kg_eval_kernel<V, A, APT, TPC, RES, MODE>, smem, eval_threads(MODE)};
 }
 
 // Variants: complex64 resident with full 4096-amplitude tiles (specialised loop), complex64
@@ -2597,6 +2655,8 @@ static KernelChoice pick(int prec, int variant, int t_bits) {
   return choice<float2, float, 8, 1, false, kModeGeneric>(t_bits);
 }
 
+int eval_kernel_threads(int prec, int variant, int t_bits) { return pick(prec, variant, t_bits).threads; }
+
 int max_tile_bits(int prec) { return prec == KG_PREC_C128 ? kLogNT + 2 : kLogNT + 3; }
 int resident_tiles_per_cta(int prec) { return prec == KG_PREC_C128 ? 0 : 2; }
 
@@ -2606,7 +2666,7 @@ cudaError_t launch_eval_kernel(int prec, int variant, const EvalParams& p, int c
   if (err != cudaSuccess) return err;
   EvalParams pc = p;
   void* args[] = {&pc};
-  return cudaLaunchCooperativeKernel(k.fn, dim3(ctas), dim3(kThreads), args, k.smem, stream);
+  return cudaLaunchCooperativeKernel(k.fn, dim3(ctas), dim3(k.threads), args, k.smem, stream);
 }
 
 cudaError_t eval_kernel_max_ctas(int prec, int variant, int t_bits, int* out) {
@@ -2614,7 +2674,7 @@ cudaError_t eval_kernel_max_ctas(int prec, int variant, int t_bits, int* out) {
   cudaError_t err = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, kThreads, k.smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem);
   if (err != cudaSuccess) return err;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

@@ -21,6 +21,9 @@ cudaError_t launch_eval_kernel(int prec, int variant, const EvalParams& p, int c
 // Largest co-resident grid of the evaluation kernel for a tile of 2^t_bits amplitudes.
 cudaError_t eval_kernel_max_ctas(int prec, int variant, int t_bits, int* out);
 
+// Threads per CTA of that kernel (kThreads, plus a control warp for the resident 4096-tile loop).
+int eval_kernel_threads(int prec, int variant, int t_bits);
+
 // Largest tile (log2 amplitudes) of a precision, and tiles a CTA can hold resident (0: none).
 int max_tile_bits(int prec);
 int resident_tiles_per_cta(int prec);

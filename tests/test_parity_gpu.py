@@ -207,6 +207,44 @@ def test_sx_control_on_other_sites(site):
     check("c128", F, g, F_ref, g_ref)
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_near_invariant_subspace_in_every_slice(prec):
+    # psi0 = |0...0> (an eigenstate of H0 and of the Sz edge control) plus 1 % of a random state:
+    # b_1^2 = ||H v_0||^2 - alpha_0^2 cancels to ~1e-4 of ||H v_0||^2 in every slice, so b_1 is
+    # formed from ||W_1 - alpha_0 v_0||^2 explicitly before step 1 goes on (complex64 resident
+    # loop: 2^14 amplitudes in 4096-amplitude tiles, two per CTA).
+    L, N, m, dt = 14, 6, 12, 0.05
+    D = 1 << L
+    mask = 1 | (1 << (L - 1))
+    rng = np.random.default_rng(41)
+    u = rng.uniform(-1, 1, N)
+    r = (rng.standard_normal(D) + 1j * rng.standard_normal(D)) / np.sqrt(2 * D)
+    psi0 = 0.01 * r
+    psi0[0] += 1.0
+    psi0 /= np.linalg.norm(psi0)
+    f = 0.5 * r  # a target with a share of the same random state: the gradient is O(1 %)
+    f[0] += 1.0
+    f /= np.linalg.norm(f)
+    ch = oracle.Chain(L, 1.0, 0.6, "sz", hc_mask=mask, hc_amp=1.0)
+    W1 = ch.apply_H(u[0], psi0)
+    a0 = np.vdot(psi0, W1).real
+    assert (np.vdot(W1, W1).real - a0 * a0) / np.vdot(W1, W1).real < 1e-3  # the identity for b_1^2 cancels
+    F_ref, g_ref, _ = oracle.evaluate(ch, u, dt, m, psi0, f, "centered")
+    A = api()
+    tb = 12 if prec == "c64" else 0
+    F, g, rep = run_gpu(A.ChainSpec(L, 1.0, 0.6, "sz", hc_mask=mask, hc_amp=1.0),
+                        A.Options(N, dt, m, prec=prec, tile_bits=tb), u, psi0, f)
+    # G_j = 2 dt Im <chi_j|Hc|psi_j> is ~2e-4 here, the imaginary part of an overlap of modulus
+    # ~0.8: complex64 rounding of that overlap (~1e-7 of it) is ~1e-4 of G, so the complex64
+    # gradient is held to 1e-3 (a wrong step-1 basis vector moves G by O(1) of itself).
+    tf, tg = TOL[prec]
+    assert rel(F, F_ref) <= tf, (F, F_ref)
+    assert nrel(g, g_ref) <= (1e-3 if prec == "c64" else tg), nrel(g, g_ref)
+    assert rep["status"] == 0 and rep["breakdowns"] == 0
+    if prec == "c64":
+        assert rep["tile_bits"] == 12 and rep["threads"] == 544  # 16 worker warps and the control warp
+
+
 def test_paper_control_sz_edges():
     # Sec. 3.1's control Hc = (J/2)(sigma^z_1 + sigma^z_L) = J (Sz_1 + Sz_L)
     L, N, m = 9, 12, 10
