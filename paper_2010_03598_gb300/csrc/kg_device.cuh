@@ -906,4 +906,87 @@ __device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const doubl
   c_im = yi;
 }
 
+// 1/p as float-float values (high part, remainder), p = 0..40, formed by the compiler.
+#define KG_IFF(p) {(float)(1.0 / (p)), (float)(1.0 / (p) - (double)(float)(1.0 / (p)))}
+__device__ __constant__ float2 kInvFF[41] = {
+    {0.f, 0.f}, KG_IFF(1),  KG_IFF(2),  KG_IFF(3),  KG_IFF(4),  KG_IFF(5),  KG_IFF(6),  KG_IFF(7),  KG_IFF(8),
+    KG_IFF(9),  KG_IFF(10), KG_IFF(11), KG_IFF(12), KG_IFF(13), KG_IFF(14), KG_IFF(15), KG_IFF(16), KG_IFF(17),
+    KG_IFF(18), KG_IFF(19), KG_IFF(20), KG_IFF(21), KG_IFF(22), KG_IFF(23), KG_IFF(24), KG_IFF(25), KG_IFF(26),
+    KG_IFF(27), KG_IFF(28), KG_IFF(29), KG_IFF(30), KG_IFF(31), KG_IFF(32), KG_IFF(33), KG_IFF(34), KG_IFF(35),
+    KG_IFF(36), KG_IFF(37), KG_IFF(38), KG_IFF(39), KG_IFF(40)};
+#undef KG_IFF
+
+__device__ __forceinline__ FF ff_from_double(double d) {
+  const float hi = (float)d;
+  return {hi, (float)(d - (double)hi)};
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ FF ff_shfl_up(FF a) {
+  return {__shfl_up_sync(0xffffffffu, a.hi, 1), __shfl_up_sync(0xffffffffu, a.lo, 1)};
+}
+__device__ __forceinline__ FF ff_shfl_down(FF a) {
+  return {__shfl_down_sync(0xffffffffu, a.hi, 1), __shfl_down_sync(0xffffffffu, a.lo, 1)};
+}
+
+// The same exponential as tridiag_expv_e1 (same split into s steps, same term count K for `tol`,
+// same series) in float-float arithmetic (about 44 significant bits) instead of FP64, for the
+// complex64 path, whose coefficients are rounded to FP32 afterwards: FP32 instructions run far
+// faster than FP64 ones on this GPU.  The FP64 tridiagonal is split into float-float once; the
+// terms are formed as t_p = (A t_{p-1}) / p, which keeps them within the FP32 range.
+__device__ __forceinline__ void tridiag_expv_e1_ff(const double* alpha, const double* beta, const float* alpha_f,
+                                                   const float* beta_f, int n, double tau, float tau_f, double tol,
+                                                   double& c_re, double& c_im, float& tnorm) {
+  const int lane = threadIdx.x & 31;
+  const bool in = lane < n;
+  float row = 0.f;
+  if (in) row = fabsf(tau_f) * (fabsf(alpha_f[lane]) + (lane >= 1 ? beta_f[lane] : 0.f) +
+                                (lane + 1 < n ? beta_f[lane + 1] : 0.f));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) row = fmaxf(row, __shfl_xor_sync(0xffffffffu, row, o));
+  tnorm = row;
+  int s = (int)ceilf(row * 1.0001f * 0.25f);
+  if (s < 1) s = 1;
+  const double h = (s == 1) ? tau : tau / (double)s;
+  const FF ha = ff_from_double(in ? h * alpha[lane] : 0.0);  // rows of A = h T
+  const FF hbl = ff_from_double((in && lane >= 1) ? h * beta[lane] : 0.0);
+  const FF hbh = ff_from_double((lane + 1 < n) ? h * beta[lane + 1] : 0.0);
+  const float r = row * 1.0001f / (float)s;
+  int K = 0;
+  {
+    float rem = r;
+    while (K < 40 && rem >= (float)tol) { ++K; rem = rem * r / (float)(K + 1); }
+  }
+  FF yr{(lane == 0) ? 1.f : 0.f, 0.f}, yi{0.f, 0.f};
+  for (int st = 0; st < s; ++st) {
+    const bool cplx = (st > 0);
+    FF pr = yr, pi = yi;  // t_p = A^p y / p!
+    FF ar = yr, ai = yi;  // accumulated result
+    for (int k = 1; k <= K; ++k) {
+      const float2 wf = kInvFF[k];
+      const FF w{wf.x, wf.y};
+      {
+        const FF m1 = ff_shfl_up(pr), p1 = ff_shfl_down(pr);
+        pr = ff_mul(w, ff_add(ff_add(ff_mul(hbl, m1), ff_mul(ha, pr)), ff_mul(hbh, p1)));
+      }
+      if (cplx) {
+        const FF m1 = ff_shfl_up(pi), p1 = ff_shfl_down(pi);
+        pi = ff_mul(w, ff_add(ff_add(ff_mul(hbl, m1), ff_mul(ha, pi)), ff_mul(hbh, p1)));
+      }
+      const FF tr = pr;
+      const FF ti = cplx ? pi : FF{0.f, 0.f};
+      // (-i)^k: k%4 == 1 -> -i, 2 -> -1, 3 -> +i, 0 -> +1, applied to (pr + i pi)
+      switch (k & 3) {
+        case 0: ar = ff_add(ar, tr); if (cplx) ai = ff_add(ai, ti); break;
+        case 1: if (cplx) ar = ff_add(ar, ti); ai = ff_add(ai, ff_neg(tr)); break;
+        case 2: ar = ff_add(ar, ff_neg(tr)); if (cplx) ai = ff_add(ai, ff_neg(ti)); break;
+        default: if (cplx) ar = ff_add(ar, ff_neg(ti)); ai = ff_add(ai, tr); break;
+      }
+    }
+    yr = ar;
+    yi = ai;
+  }
+  c_re = ff_to_double(yr);
+  c_im = ff_to_double(yi);
+}
+
 }  // namespace kg

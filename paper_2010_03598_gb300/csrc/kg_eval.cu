@@ -98,6 +98,7 @@ struct SmemSlice {
   Group grp;  // the group's barrier state while the resident loop runs (written by thread 0)
   float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
   float4 slotbuf[2 * kSlotRanks];  // the group's reduction slots, prefetched by warp 0
+  int recomb_pre;  // the Lanczos loop has issued the recombination's first copies (complex64)
   int ctl_cmd;  // control warp: the step whose sums were handed over (| kCtlLast), or kCtlExit
   int ctl_ok;   // control warp: the group barrier passed (0: aborted or timed out)
   unsigned ff_e_set;
@@ -735,11 +736,13 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
   // its own copies.  The first copies do not depend on c: they go out before the exponential.
   float4* stg = reinterpret_cast<float4*>(c.sv[0]);  // [kRecombDepth][2 tiles x 4][kThreads]
   size_t rb[2] = {0, 0};
+  bool pre = false;
   if constexpr (WBASIS) {
     rb[0] = (c.n_own > 0) ? c.tile_base(0) : 0;
     rb[1] = (c.n_own > 1) ? c.tile_base(1) : 0;
     wsync();  // every thread is done with the Lanczos loop's shared memory
-    if (tid >= 32) {  // warp 0 issues its copies after the exponential
+    pre = ss.recomb_pre != 0;  // the Lanczos loop has issued the first copies already
+    if (tid >= 32 && !pre) {  // warp 0 issues its copies after the exponential
       for (int s = 0; s < kRecombDepth; ++s) {
         if (s < meff) {  // newest basis vector first (see the loop below)
           const int ks = meff - 1 - s;
@@ -755,8 +758,12 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
     double cr = 0.0, ci = 0.0;
     float tnorm = 0.f;
     const double tol = (sizeof(R) == 4) ? 1e-13 : 1e-18;
-    if (meff > 0)
-      tridiag_expv_e1(ss.alpha, ss.beta, ss.alpha_f, ss.beta_f, meff, tau, (float)tau, tol, cr, ci, tnorm);
+    if (meff > 0) {
+      if constexpr (sizeof(R) == 4)
+        tridiag_expv_e1_ff(ss.alpha, ss.beta, ss.alpha_f, ss.beta_f, meff, tau, (float)tau, tol, cr, ci, tnorm);
+      else
+        tridiag_expv_e1(ss.alpha, ss.beta, ss.alpha_f, ss.beta_f, meff, tau, (float)tau, tol, cr, ci, tnorm);
+    }
     if (tid < meff) {
       // basis slot 0 is psi itself (unnormalised); slots k >= 1 hold normalised v_k
       const double f = (tid == 0) ? 1.0 : nrm_src;
@@ -783,26 +790,33 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
       // ||psi|| sum_k c_k v_k = sum_k e_k W_k + (s_0/||psi||) psi, where, from the top,
       // s_{m-1} = ||psi|| c_{m-1}, e_k = s_k / b_k, s_{k-1} = ||psi|| c_{k-1} - e_k alpha_{k-1}.
       // FP32 suffices: the coefficients only combine complex64 vectors.
+      // Lane k holds ||psi|| c_k (s_k once the lanes above have passed e_{k+1} down); the
+      // recurrence runs down the lanes, one shuffle per step.
       __syncwarp();
-      if (tid == 0 && meff > 1) {
-        float sr = ss.coef_re_f[meff - 1], si = ss.coef_im_f[meff - 1];  // s_{m-1} = ||psi|| c_{m-1}
-        for (int k = meff - 1; k >= 2; --k) {
-          const float ib = 1.f / ss.beta_f[k], al = ss.alpha_f[k - 1];
-          const float er = sr * ib, ei = si * ib;
-          ss.coef_re_f[k] = er;
-          ss.coef_im_f[k] = ei;
-          sr = ss.coef_re_f[k - 1] - er * al;  // ||psi|| c_{k-1} - e_k alpha_{k-1}
-          si = ss.coef_im_f[k - 1] - ei * al;
+      if (meff > 1) {
+        const bool own = tid < meff;
+        float sr = own ? ss.coef_re_f[tid] : 0.f, si = own ? ss.coef_im_f[tid] : 0.f;
+        const float ib = (own && tid >= 1) ? 1.f / ss.beta_f[tid] : 0.f;
+        const float al = own ? ss.alpha_f[tid] : 0.f;  // alpha_k on lane k
+        for (int k = meff - 1; k >= 1; --k) {
+          const float er = sr * ib, ei = si * ib;  // e_k on lane k
+          const float erb = __shfl_sync(0xffffffffu, er, k), eib = __shfl_sync(0xffffffffu, ei, k);
+          if (tid == k) {
+            ss.coef_re_f[k] = er;
+            ss.coef_im_f[k] = ei;
+          } else if (tid == k - 1) {
+            if (k >= 2) {
+              sr = sr - erb * al;  // ||psi|| c_{k-1} - e_k alpha_{k-1}
+              si = si - eib * al;
+            } else {
+              // psi coefficient s_0 / ||psi|| = c_0 - e_1 alpha_0 / ||psi|| (slot 0 held c_0)
+              ss.coef_re_f[0] = sr - erb * al * ss.f_ib0;
+              ss.coef_im_f[0] = si - eib * al * ss.f_ib0;
+            }
+          }
         }
-        const float ib = 1.f / ss.beta_f[1], al = ss.alpha_f[0];
-        const float er = sr * ib, ei = si * ib;  // e_1
-        ss.coef_re_f[1] = er;
-        ss.coef_im_f[1] = ei;
-        // psi coefficient s_0 / ||psi|| = c_0 - e_1 alpha_0 / ||psi|| (slot 0 held c_0)
-        ss.coef_re_f[0] -= er * al * ss.f_ib0;
-        ss.coef_im_f[0] -= ei * al * ss.f_ib0;
       }
-      for (int s = 0; s < kRecombDepth; ++s) {
+      for (int s = 0; s < kRecombDepth && !pre; ++s) {
         if (s < meff) {  // newest basis vector first (see the loop below)
           const int ks = meff - 1 - s;
           recomb_issue(ks == 0 ? src : c.basis_slot(ks), rb, c.n_own, stg + (size_t)s * 8 * kThreads);
@@ -812,6 +826,7 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
     }
   }
   wsync();
+  if (WBASIS && tid == 0) ss.recomb_pre = 0;  // every thread has read it
   c.mark(4);
   if (tid == 0 && meff > 0 && !interior) c.breakdowns += ss.broke ? 1 : 0;
   // ---- recombination dst = sum_k coef_k (basis slot k) (+ fused norms / overlaps)
@@ -1478,18 +1493,21 @@ __device__ __forceinline__ void stv4_hint(float4* p, float4 v, unsigned long lon
                : "memory");
 }
 
-// Cross-tile part of H W for one tile in the pair layout (table entries i0 .. i1), added into h:
-// h[a] += wgt W[partner] for the own amplitude a = 2g + x at pair tid + 512 g.  A whole-tile entry
-// feeds every own pair, element for element; a half entry (the bond between the top in-tile bit
-// and the lowest tile bit) feeds the own half (bit 11 = bit 1 of g) from pairs tid + 512 g' of the
-// 1024-pair half block.  Two entries in flight.
-__device__ __forceinline__ void partner_acc(const SmemSlice& ss, const float2* pv, int i0, int i1, float2 (&h)[8]) {
+// Cross-tile part of H W for one tile in the pair layout (table entries i0 .. i1), added to the
+// in-tile part parked in tensor memory at taddr, which is parked there again (the store is not
+// waited for): h[a] += wgt W[partner] for the own amplitude a = 2g + x at pair tid + 512 g.  A
+// whole-tile entry feeds every own pair, element for element; a half entry (the bond between the
+// top in-tile bit and the lowest tile bit) feeds the own half (bit 11 = bit 1 of g) from pairs
+// tid + 512 g' of the 1024-pair half block.  Two entries in flight; the parked part is loaded once
+// the first entries' loads are under way.  Earlier tensor-memory stores to taddr are waited for.
+__device__ __forceinline__ void partner_acc(const SmemSlice& ss, const float2* pv, int i0, int i1, uint32_t taddr) {
   constexpr int G = 2;
   const int tid = threadIdx.x;
   const float hxy = ss.r.hxy, cu_sx = ss.r.cusx;
-  for (int ib = i0; ib < i1; ib += G) {
-    float4 q[G][4];
-    float wq[G];
+  if (i0 >= i1) return;  // no block leaves this tile: the parked part is complete
+  float4 q[G][4];
+  float wq[G];
+  auto load = [&](int ib) {
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const int i = ib + u;
@@ -1504,6 +1522,12 @@ __device__ __forceinline__ void partner_acc(const SmemSlice& ss, const float2* p
         q[u][g] = ((hm >> g) & 1u) ? ldv4(sb + 512 * gs) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+  };
+  load(i0);
+  float2 h[8];
+  tmem_st_wait();
+  tmem_ld8c(taddr, h);  // the parked in-tile part, while the first loads are in flight
+  for (int ib = i0;;) {
 #pragma unroll
     for (int u = 0; u < G; ++u)
 #pragma unroll
@@ -1511,7 +1535,11 @@ __device__ __forceinline__ void partner_acc(const SmemSlice& ss, const float2* p
         h[2 * g] = f2fma(f2(wq[u]), lo2(q[u][g]), h[2 * g]);
         h[2 * g + 1] = f2fma(f2(wq[u]), hi2(q[u][g]), h[2 * g + 1]);
       }
+    ib += G;
+    if (ib >= i1) break;
+    load(ib);
   }
+  tmem_st8c_nowait(taddr, h);
 }
 
 // In-tile part of H_j W for the own pairs of tile cc, from shared memory only: the bonds inside
@@ -1749,14 +1777,8 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
       if (prof) prof_mark(ss, 2);
     }
     // ---- 2. H W_k of both tiles: the parked in-tile part plus the partner blocks, parked again
-    tmem_st_wait();
 #pragma unroll 1
-    for (int cc = 0; cc < n_own; ++cc) {
-      float2 h[8];
-      tmem_ld8c(tP + 16u * cc, h);
-      partner_acc(ss, vec, ss.ct_start[cc], ss.ct_start[cc + 1], h);
-      tmem_st8c_nowait(tP + 16u * cc, h);
-    }
+    for (int cc = 0; cc < n_own; ++cc) partner_acc(ss, vec, ss.ct_start[cc], ss.ct_start[cc + 1], tP + 16u * cc);
     if (prof) prof_mark(ss, 0);
     // ---- 3. alpha_{k-1}, b_k and the scalars of step k (formed by the control warp)
     if (k > 0) {
@@ -1849,11 +1871,28 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
   }
   tmem_st_wait();  // every store of v_k, H v_k has completed
   if (done) {  // the last step's sums: alpha_{m-1}, b_m (error indicator), formed by the control warp
+    // Meanwhile the recombination's first copies go out (the own tiles of the newest basis
+    // vectors, which this CTA stored itself; they do not depend on the last sums), into the
+    // shared memory the loop no longer needs.
+    wsync();
+    {
+      const size_t rb[2] = {ss.r.tbase[0], ss.r.tbase[1]};
+      float4* stg = reinterpret_cast<float4*>(c.sv[0]);
+      for (int s = 0; s < kRecombDepth; ++s) {
+        if (s < m) {
+          const int ks = m - 1 - s;
+          recomb_issue(ks == 0 ? src : ss.r.basis + (size_t)(ks - 1) * ss.r.D, rb, n_own,
+                       stg + (size_t)s * 8 * kThreads);
+        }
+        cp_async_commit();
+      }
+      if (tid == 0) ss.recomb_pre = 1;
+    }
     nbar_sync(kBarGroup, kCtlThreads);
     nbar_sync(kBarScal, kCtlThreads);
-    if (!ss.ctl_ok) return false;
-    if (ss.code1 == 2) {
-      if (tid == 0) flag_nonfinite(p);
+    if (!ss.ctl_ok || ss.code1 == 2) {
+      cp_async_wait<0>();
+      if (ss.ctl_ok && tid == 0) flag_nonfinite(p);
       return false;
     }
   }
@@ -2400,6 +2439,7 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
   for (int i = 0; i < 8; ++i)
     if (c.prof_on && threadIdx.x == 0) ss.prof_acc[i] = 0;
   const bool lead = (rank == 0 && threadIdx.x == 0);
+  if (threadIdx.x == 0) ss.recomb_pre = 0;
 
   // ---- forward sweep (Alg. "Basic GRAPE", step 4)
   double nrm_prev;
