@@ -906,14 +906,15 @@ __device__ __forceinline__ void tridiag_expv_e1(const double* alpha, const doubl
   c_im = yi;
 }
 
-// 1/p as float-float values (high part, remainder), p = 0..40, formed by the compiler.
+// 1/p as float-float values (high part, remainder), p = 1..41, formed by the compiler (an FP32
+// division is a ~85-cycle subroutine on this GPU; these products replace it).
 #define KG_IFF(p) {(float)(1.0 / (p)), (float)(1.0 / (p) - (double)(float)(1.0 / (p)))}
-__device__ __constant__ float2 kInvFF[41] = {
+__device__ __constant__ float2 kInvFF[42] = {
     {0.f, 0.f}, KG_IFF(1),  KG_IFF(2),  KG_IFF(3),  KG_IFF(4),  KG_IFF(5),  KG_IFF(6),  KG_IFF(7),  KG_IFF(8),
     KG_IFF(9),  KG_IFF(10), KG_IFF(11), KG_IFF(12), KG_IFF(13), KG_IFF(14), KG_IFF(15), KG_IFF(16), KG_IFF(17),
     KG_IFF(18), KG_IFF(19), KG_IFF(20), KG_IFF(21), KG_IFF(22), KG_IFF(23), KG_IFF(24), KG_IFF(25), KG_IFF(26),
     KG_IFF(27), KG_IFF(28), KG_IFF(29), KG_IFF(30), KG_IFF(31), KG_IFF(32), KG_IFF(33), KG_IFF(34), KG_IFF(35),
-    KG_IFF(36), KG_IFF(37), KG_IFF(38), KG_IFF(39), KG_IFF(40)};
+    KG_IFF(36), KG_IFF(37), KG_IFF(38), KG_IFF(39), KG_IFF(40), KG_IFF(41)};
 #undef KG_IFF
 
 __device__ __forceinline__ FF ff_from_double(double d) {
@@ -953,8 +954,9 @@ __device__ __forceinline__ void tridiag_expv_e1_ff(const double* alpha, const do
   const float r = row * 1.0001f / (float)s;
   int K = 0;
   {
+    const float tolf = (float)tol;
     float rem = r;
-    while (K < 40 && rem >= (float)tol) { ++K; rem = rem * r / (float)(K + 1); }
+    while (K < 40 && rem >= tolf) { ++K; rem = rem * r * kInvFF[K + 1].x; }
   }
   FF yr{(lane == 0) ? 1.f : 0.f, 0.f}, yi{0.f, 0.f};
   for (int st = 0; st < s; ++st) {

@@ -780,7 +780,7 @@ __device__ __forceinline__ bool finish_slice(Ctx<V>& c, const V* src, double nrm
       if (tid == 0) cm *= ss.f_bk0;
       if (cm == 0.f && !broke) {
         cm = ss.f_bk0;
-        for (int i = 1; i < meff; ++i) cm *= tnorm / (float)i;
+        for (int i = 1; i < meff; ++i) cm *= tnorm * kInvFF[i].x;  // / i
       }
       const float err = broke ? 0.f : ss.f_beta_m * cm;
       if (!interior) c.err_max = fmax(c.err_max, (double)err);  // lane meff-1 of warp 0 keeps the maximum
@@ -1498,10 +1498,10 @@ __device__ __forceinline__ void stv4_hint(float4* p, float4 v, unsigned long lon
 // waited for): h[a] += wgt W[partner] for the own amplitude a = 2g + x at pair tid + 512 g.  A
 // whole-tile entry feeds every own pair, element for element; a half entry (the bond between the
 // top in-tile bit and the lowest tile bit) feeds the own half (bit 11 = bit 1 of g) from pairs
-// tid + 512 g' of the 1024-pair half block.  Two entries in flight; the parked part is loaded once
+// tid + 512 g' of the 1024-pair half block.  Three entries in flight; the parked part is loaded once
 // the first entries' loads are under way.  Earlier tensor-memory stores to taddr are waited for.
 __device__ __forceinline__ void partner_acc(const SmemSlice& ss, const float2* pv, int i0, int i1, uint32_t taddr) {
-  constexpr int G = 2;
+  constexpr int G = 3;
   const int tid = threadIdx.x;
   const float hxy = ss.r.hxy, cu_sx = ss.r.cusx;
   if (i0 >= i1) return;  // no block leaves this tile: the parked part is complete

@@ -550,8 +550,12 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
       sec_record(sm, -1, 3);
       sm.abort = 1;
     }
-    if (meff > 0 && sane)
-      tridiag_expv_e1(sm.alpha, sm.beta, sm.alpha_f, sm.beta_f, meff, tw, (float)tw, etol, cr, ci, tnorm);
+    if (meff > 0 && sane) {
+      if constexpr (F32)  // float-float: FP64 instructions are slow on this GPU (see tridiag_expv_e1_ff)
+        tridiag_expv_e1_ff(sm.alpha, sm.beta, sm.alpha_f, sm.beta_f, meff, tw, (float)tw, etol, cr, ci, tnorm);
+      else
+        tridiag_expv_e1(sm.alpha, sm.beta, sm.alpha_f, sm.beta_f, meff, tw, (float)tw, etol, cr, ci, tnorm);
+    }
     if (k < meff) {
       sm.coef_d[w][0][k] = cr * nrm;
       sm.coef_d[w][1][k] = ci * nrm;
@@ -833,10 +837,17 @@ __device__ __forceinline__ void sec_eval(const SectorParams& p, int b, SecSmem& 
   sec_sync();
 }
 
-// Blocks of up to 256 threads are held to 128 registers a thread, so that two CTAs (two pulses)
-// share an SM and hide each other's barrier and FP64 latency.
+// CTAs (pulses) per SM the register allocation is sized for.  A pulse is a chain of latencies
+// (block barriers, FP64 on warp 0), so pulses sharing an SM hide each other's: complex64 blocks of
+// 128 threads are held to 64 registers a thread, eight pulses per SM (a few spills; measured 1.9x the
+// pulses/s of three per SM at D = 511); other blocks of up to 256 threads to 128 registers, two per SM.
+template <class V, int NT>
+constexpr int sec_min_blocks() {
+  return (NT == 128 && sizeof(V) == sizeof(float2)) ? 8 : (NT <= 256) ? 2 : 1;
+}
+
 template <class V, int NT, int RPT>
-__global__ void __launch_bounds__(NT, (NT <= 256) ? 2 : 1) kg_sector_kernel(const __grid_constant__ SectorParams p) {
+__global__ void __launch_bounds__(NT, (sec_min_blocks<V, NT>())) kg_sector_kernel(const __grid_constant__ SectorParams p) {
   extern __shared__ __align__(16) unsigned char sec_dyn[];
   __shared__ SecSmem sm;
   const int Dp = (p.D + 15) & ~15;
