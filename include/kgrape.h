@@ -362,8 +362,11 @@ kg_status kg_sector_destroy(kg_sector_handle* handle);
 /* Test hook for failure detection.  kind 1: in the next launch, CTA 0 does not arrive at
  * the first group barrier (a member that never joins); the other CTAs' waits, and its own,
  * run out after the wait limit and the launch ends with KG_ERR_TIMEOUT (read by kg_sync).
- * Only multi-CTA launches have a group barrier.  The hook applies to one launch and then
- * clears itself; kind 0 clears it.  Nothing faults, traps or hangs. */
+ * kind 2: the same at the barrier of the first Lanczos step instead (in the resident complex64
+ * loop of 4096-amplitude tiles, the barrier its control warp arrives at and waits on).  Only
+ * multi-CTA launches have a group barrier.  The hook applies to one launch and then clears
+ * itself; kind 0 clears it.  Nothing faults, traps or hangs.  Returns KG_ERR_INVALID_ARG for
+ * another kind. */
 kg_status kg_debug_set_fault(int32_t kind);
 
 #ifdef __cplusplus

@@ -243,7 +243,7 @@ kg_status kg_set_wait_limit_ns(int64_t ns) {
 }
 
 kg_status kg_debug_set_fault(int32_t kind) {
-  if (kind != 0 && kind != 1) return fail(KG_ERR_INVALID_ARG, "fault kind must be 0 or 1");
+  if (kind < 0 || kind > 2) return fail(KG_ERR_INVALID_ARG, "fault kind must be 0, 1 or 2");
   g_debug_fault.store(kind);
   return KG_OK;
 }

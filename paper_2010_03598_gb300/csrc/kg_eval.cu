@@ -2444,6 +2444,7 @@ __device__ __noinline__ bool run_eval(const EvalParams& p, int rank, int size, S
   // ---- forward sweep (Alg. "Basic GRAPE", step 4)
   double nrm_prev;
   if (!init_state<V>(c, fwd_slot<V>(c, 0), nrm_prev)) return false;
+  if (p.debug_fault == 2 && rank == 0) c.g.skip_arrival = 1;  // at the first Lanczos step's barrier
   if (lead) p.nrm[0] = nrm_prev;
   c.mark(6);
   double2 beta = make_double2(0.0, 0.0);

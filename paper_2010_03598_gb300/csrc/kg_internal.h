@@ -54,7 +54,7 @@ struct EvalParams {
   int* ctrl;                // [kCtrlStatus, kCtrlAbort]
   unsigned long long* iring;  // [kIRing][4] fixed-point group sums (zeroed before each launch), or null
   long long wait_limit_ns;
-  int debug_fault;          // 1: CTA 0 skips its arrival at the first group barrier
+  int debug_fault;          // 1: CTA 0 skips its arrival at the first group barrier; 2: at the first Lanczos step's
   int reorth;               // full CGS2 re-orthogonalisation of every Lanczos step
   long long* prof;          // [8] phase cycles of CTA 0, or null
 };

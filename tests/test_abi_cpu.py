@@ -149,6 +149,8 @@ def test_wait_limit_and_fault_hook_arguments(lib):
     assert lib.kg_set_wait_limit_ns(0) == _abi.KG_ERR_INVALID_ARG
     assert lib.kg_set_wait_limit_ns(2_000_000_000) == _abi.KG_OK
     assert lib.kg_debug_set_fault(3) == _abi.KG_ERR_INVALID_ARG
+    assert lib.kg_debug_set_fault(-1) == _abi.KG_ERR_INVALID_ARG
+    assert lib.kg_debug_set_fault(2) == _abi.KG_OK
     assert lib.kg_debug_set_fault(0) == _abi.KG_OK
 
 

@@ -402,6 +402,33 @@ def test_member_that_never_arrives_times_out_cleanly():
     eng.close()
 
 
+def test_member_that_skips_a_lanczos_step_arrival_times_out_cleanly():
+    # The same fault at the first Lanczos step's barrier of the resident complex64 loop (2^14
+    # amplitudes, 4096-amplitude tiles, two CTAs): CTA 0's control warp does not arrive, every
+    # control warp's wait runs out or sees the abort, answers its workers at both named barriers,
+    # and the launch ends with KG_ERR_TIMEOUT; the next launch on the same engine is clean.
+    A = api()
+    from paper_2010_03598_gb300 import _abi
+    L = 14
+    eng = A.KGrape(A.ChainSpec(L), A.Options(3, 0.1, 8, prec="c64", tile_bits=12))
+    rng = np.random.default_rng(2)
+    ut, pt, ft = to_dev(rng.uniform(-1, 1, 3), W.neel_state(L), W.draw_target(rng, 1 << L))
+    try:
+        A.set_wait_limit_ns(50_000_000)
+        _abi.check(_abi.lib().kg_debug_set_fault(2), "kg_debug_set_fault")
+        eng.evaluate(ut, pt, ft)
+        with pytest.raises(_abi.KGrapeError) as ei:
+            eng.sync()
+        assert ei.value.status == _abi.KG_ERR_TIMEOUT
+    finally:
+        A.set_wait_limit_ns(2_000_000_000)
+        _abi.lib().kg_debug_set_fault(0)
+    eng.evaluate(ut, pt, ft)
+    rep = eng.sync()
+    assert rep["status"] == 0 and rep["threads"] == 544 and rep["ctas"] == 2
+    eng.close()
+
+
 # ------------------------------------------------------------------ adjoint vs finite differences
 def test_L20_adjoint_gradient_vs_central_finite_differences():
     # Central FD of F (FP64 path, step 1e-4) at 16 seeded slice indices.  The centred gradient
