@@ -230,66 +230,8 @@ __device__ __forceinline__ void tmem_ld8f(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Split tensor-memory accesses: tmem_ld16_issue starts two 16-column loads (v and H v of a
-// tile) and returns the registers they fill; tmem_ld_wait waits for them and passes the same
-// registers through, so that no instruction can read them before the wait.  tmem_st16x2_nowait
-// starts two stores and leaves their completion to a later tmem_st_wait (before the columns are
-// read again or freed).
-struct TmemRaw32 {
-  uint32_t r[32];
-};
-__device__ __forceinline__ TmemRaw32 tmem_ld16_issue(uint32_t ta, uint32_t tb) {
-  TmemRaw32 t;
-  uint32_t* r = t.r;
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%32];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%33];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(ta), "r"(tb)
-      : "memory");
-  return t;
-}
-__device__ __forceinline__ void tmem_ld_wait(TmemRaw32& t, float2 (&a)[8], float2 (&b)[8]) {
-  uint32_t* r = t.r;
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
-                 "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]),
-                 "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
-                 "+r"(r[30]), "+r"(r[31])
-               :
-               : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
-    b[i] = make_float2(__uint_as_float(r[16 + 2 * i]), __uint_as_float(r[16 + 2 * i + 1]));
-  }
-}
-__device__ __forceinline__ void tmem_st16x2_nowait(uint32_t ta, uint32_t tb, const float2 (&a)[8],
-                                                   const float2 (&b)[8]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17};\n"
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], {%18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
-      "%31, %32, %33};\n" ::"r"(ta),
-      "r"(tb), "r"(__float_as_uint(a[0].x)), "r"(__float_as_uint(a[0].y)), "r"(__float_as_uint(a[1].x)),
-      "r"(__float_as_uint(a[1].y)), "r"(__float_as_uint(a[2].x)), "r"(__float_as_uint(a[2].y)),
-      "r"(__float_as_uint(a[3].x)), "r"(__float_as_uint(a[3].y)), "r"(__float_as_uint(a[4].x)),
-      "r"(__float_as_uint(a[4].y)), "r"(__float_as_uint(a[5].x)), "r"(__float_as_uint(a[5].y)),
-      "r"(__float_as_uint(a[6].x)), "r"(__float_as_uint(a[6].y)), "r"(__float_as_uint(a[7].x)),
-      "r"(__float_as_uint(a[7].y)), "r"(__float_as_uint(b[0].x)), "r"(__float_as_uint(b[0].y)),
-      "r"(__float_as_uint(b[1].x)), "r"(__float_as_uint(b[1].y)), "r"(__float_as_uint(b[2].x)),
-      "r"(__float_as_uint(b[2].y)), "r"(__float_as_uint(b[3].x)), "r"(__float_as_uint(b[3].y)),
-      "r"(__float_as_uint(b[4].x)), "r"(__float_as_uint(b[4].y)), "r"(__float_as_uint(b[5].x)),
-      "r"(__float_as_uint(b[5].y)), "r"(__float_as_uint(b[6].x)), "r"(__float_as_uint(b[6].y)),
-      "r"(__float_as_uint(b[7].x)), "r"(__float_as_uint(b[7].y))
-      : "memory");
-}
+// Stores that leave their completion to a later tmem_st_wait (before the columns are read again or
+// freed), and loads that wait.
 __device__ __forceinline__ void tmem_st8c_nowait(uint32_t taddr, const float2 (&v)[8]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -302,91 +244,50 @@ __device__ __forceinline__ void tmem_st8c_nowait(uint32_t taddr, const float2 (&
       "r"(__float_as_uint(v[7].y))
       : "memory");
 }
-// Half of the above: three 8-column loads (4 complex values each) under one wait, and two
-// 8-column stores without a wait.
-__device__ __forceinline__ void tmem_ld4c_x3(uint32_t ta, uint32_t tb, uint32_t tc, float2 (&a)[4], float2 (&b)[4],
-                                             float2 (&c)[4]) {
-  uint32_t r[24];
+// Four 4-column loads of this thread's TMEM row (2 complex64 values each) under one wait.
+__device__ __forceinline__ void tmem_ld2c_x4(uint32_t ta, uint32_t tb, uint32_t tc, uint32_t td, float2 (&a)[2],
+                                             float2 (&b)[2], float2 (&c)[2], float2 (&d)[2]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%24];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%25];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%26];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%17];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%18];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%19];\n"
       "tcgen05.wait::ld.sync.aligned;\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
-      : "r"(ta), "r"(tb), "r"(tc)
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb), "r"(tc), "r"(td)
       : "memory");
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
     a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
-    b[i] = make_float2(__uint_as_float(r[8 + 2 * i]), __uint_as_float(r[8 + 2 * i + 1]));
-    c[i] = make_float2(__uint_as_float(r[16 + 2 * i]), __uint_as_float(r[16 + 2 * i + 1]));
+    b[i] = make_float2(__uint_as_float(r[4 + 2 * i]), __uint_as_float(r[4 + 2 * i + 1]));
+    c[i] = make_float2(__uint_as_float(r[8 + 2 * i]), __uint_as_float(r[8 + 2 * i + 1]));
+    d[i] = make_float2(__uint_as_float(r[12 + 2 * i]), __uint_as_float(r[12 + 2 * i + 1]));
   }
 }
-__device__ __forceinline__ void tmem_st8x2_nowait(uint32_t ta, uint32_t tb, const float2 (&a)[4],
-                                                  const float2 (&b)[4]) {
+// Three 4-column stores (2 complex64 values each); completion is left to a later tmem_st_wait.
+__device__ __forceinline__ void tmem_st2c_x3_nowait(uint32_t ta, uint32_t tb, uint32_t tc, const float2 (&a)[2],
+                                                    const float2 (&b)[2], const float2 (&c)[2]) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9};\n"
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%10, %11, %12, %13, %14, %15, %16, %17};\n" ::"r"(ta),
-      "r"(tb), "r"(__float_as_uint(a[0].x)), "r"(__float_as_uint(a[0].y)), "r"(__float_as_uint(a[1].x)),
-      "r"(__float_as_uint(a[1].y)), "r"(__float_as_uint(a[2].x)), "r"(__float_as_uint(a[2].y)),
-      "r"(__float_as_uint(a[3].x)), "r"(__float_as_uint(a[3].y)), "r"(__float_as_uint(b[0].x)),
-      "r"(__float_as_uint(b[0].y)), "r"(__float_as_uint(b[1].x)), "r"(__float_as_uint(b[1].y)),
-      "r"(__float_as_uint(b[2].x)), "r"(__float_as_uint(b[2].y)), "r"(__float_as_uint(b[3].x)),
-      "r"(__float_as_uint(b[3].y))
+      "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%3, %4, %5, %6};\n"
+      "tcgen05.st.sync.aligned.32x32b.x4.b32 [%1], {%7, %8, %9, %10};\n"
+      "tcgen05.st.sync.aligned.32x32b.x4.b32 [%2], {%11, %12, %13, %14};\n" ::"r"(ta),
+      "r"(tb), "r"(tc), "r"(__float_as_uint(a[0].x)), "r"(__float_as_uint(a[0].y)), "r"(__float_as_uint(a[1].x)),
+      "r"(__float_as_uint(a[1].y)), "r"(__float_as_uint(b[0].x)), "r"(__float_as_uint(b[0].y)),
+      "r"(__float_as_uint(b[1].x)), "r"(__float_as_uint(b[1].y)), "r"(__float_as_uint(c[0].x)),
+      "r"(__float_as_uint(c[0].y)), "r"(__float_as_uint(c[1].x)), "r"(__float_as_uint(c[1].y))
       : "memory");
+}
+// One 8-column store (4 complex64 values); completion is left to a later tmem_st_wait.
+__device__ __forceinline__ void tmem_st4c_nowait(uint32_t ta, const float2 (&a)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(ta),
+               "r"(__float_as_uint(a[0].x)), "r"(__float_as_uint(a[0].y)), "r"(__float_as_uint(a[1].x)),
+               "r"(__float_as_uint(a[1].y)), "r"(__float_as_uint(a[2].x)), "r"(__float_as_uint(a[2].y)),
+               "r"(__float_as_uint(a[3].x)), "r"(__float_as_uint(a[3].y))
+               : "memory");
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
-
-// Three 16-column loads of this thread's TMEM row (8 complex64 values each) under one wait.
-__device__ __forceinline__ void tmem_ld8c_x3(uint32_t ta, uint32_t tb, uint32_t tc, float2 (&a)[8], float2 (&b)[8],
-                                             float2 (&c)[8]) {
-  uint32_t r[48];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%48];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%49];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, "
-      "%46, %47}, [%50];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
-        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
-        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
-      : "r"(ta), "r"(tb), "r"(tc)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
-    b[i] = make_float2(__uint_as_float(r[16 + 2 * i]), __uint_as_float(r[16 + 2 * i + 1]));
-    c[i] = make_float2(__uint_as_float(r[32 + 2 * i]), __uint_as_float(r[32 + 2 * i + 1]));
-  }
-}
-// Two 16-column stores under one wait.
-__device__ __forceinline__ void tmem_st8c_x2(uint32_t ta, uint32_t tb, const float2 (&a)[8], const float2 (&b)[8]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17};\n"
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], {%18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
-      "%31, %32, %33};\n"
-      "tcgen05.wait::st.sync.aligned;\n" ::"r"(ta),
-      "r"(tb), "r"(__float_as_uint(a[0].x)), "r"(__float_as_uint(a[0].y)), "r"(__float_as_uint(a[1].x)),
-      "r"(__float_as_uint(a[1].y)), "r"(__float_as_uint(a[2].x)), "r"(__float_as_uint(a[2].y)),
-      "r"(__float_as_uint(a[3].x)), "r"(__float_as_uint(a[3].y)), "r"(__float_as_uint(a[4].x)),
-      "r"(__float_as_uint(a[4].y)), "r"(__float_as_uint(a[5].x)), "r"(__float_as_uint(a[5].y)),
-      "r"(__float_as_uint(a[6].x)), "r"(__float_as_uint(a[6].y)), "r"(__float_as_uint(a[7].x)),
-      "r"(__float_as_uint(a[7].y)), "r"(__float_as_uint(b[0].x)), "r"(__float_as_uint(b[0].y)),
-      "r"(__float_as_uint(b[1].x)), "r"(__float_as_uint(b[1].y)), "r"(__float_as_uint(b[2].x)),
-      "r"(__float_as_uint(b[2].y)), "r"(__float_as_uint(b[3].x)), "r"(__float_as_uint(b[3].y)),
-      "r"(__float_as_uint(b[4].x)), "r"(__float_as_uint(b[4].y)), "r"(__float_as_uint(b[5].x)),
-      "r"(__float_as_uint(b[5].y)), "r"(__float_as_uint(b[6].x)), "r"(__float_as_uint(b[6].y)),
-      "r"(__float_as_uint(b[7].x)), "r"(__float_as_uint(b[7].y))
-      : "memory");
-}
 
 // ---------------------------------------------------------------- group context
 // A group is the set of CTAs that cooperate on one problem.  All CTAs of a group are

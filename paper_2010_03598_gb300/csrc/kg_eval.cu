@@ -47,6 +47,12 @@ constexpr int kStrDepth = 4;
 constexpr int kStrSvBufs = 2;  // tiles of v_k for the stencil (1: one more barrier per tile)
 constexpr size_t kStrSmemBytes = (size_t)kStrSvBufs * 4096 * 8 + (size_t)kStrDepth * 4 * 512 * 16;    // Lanczos partner ring: 4 x 32 KB behind the 64 KB of v_k
 constexpr int kLzMaxChunks = 2 * (1 + (kMaxL - 13) + 1);  // two tiles: bond 11, outer bonds, Sx site
+// Headline loop (lanczos_res64b): partner blocks stream through a per-thread ring of kPrRing units
+// in the shared memory behind W_k (64 KB) and the diagonal (32 KB); a unit is two 16-byte granules
+// per thread, 16 KB per CTA.  A whole-tile table entry is two units, a half entry one.
+constexpr int kPrRing = 7;
+constexpr int kLzMaxUnits = 2 * kLzMaxChunks;
+constexpr size_t kRes64bSmemBytes = (size_t)96 * 1024 + (size_t)kPrRing * 16 * 1024;
 constexpr uint32_t kTmemCols = 512;  // 128 columns per warp, 4 warps per lane quarter
 // Headline loop (lanczos_res64b): 16 worker warps and the control warp (warp 16), which meet at
 // named barriers -- kBarPost (workers arrive with a step's partial sums, the control warp waits),
@@ -64,7 +70,8 @@ struct ResCtx {
   float2* basis;     // basis slot 1 (slot k at basis + (k - 1) D)
   size_t D;
   float2* sw;        // W_k of the own tiles (shared memory)
-  float2* ring;      // partner-block ring (shared memory)
+  float2* ring;      // partner-block ring (shared memory); the headline loop: the diagonal of H_j
+  float4* pring;     // the headline loop's partner ring (shared memory)
   unsigned maskL1, mk;
   int L1, hs, hcsx, n_own, m;
   float hxy, qz, cusx, cusz, amax, bmax, bdtol;
@@ -91,6 +98,8 @@ struct SmemSlice {
   // the float-float sums of every step (for the FP64 tridiagonal), the TMEM address
   unsigned long long lmbar[kLzStages];
   unsigned ctab[kLzMaxChunks];
+  unsigned utab[kLzMaxUnits];  // headline loop: units of the partner ring (build_unit_table)
+  int n_units, n_units0;  // units of both own tiles, and of tile 0 (they come first)
   int ct_start[3];
   int first;  // the own tile computed first (more partner blocks)
   long long prof_last, prof_acc[8];  // phase timing (thread 0 of CTA 0)
@@ -1217,7 +1226,7 @@ __device__ __noinline__ bool lanczos_res64(Ctx<float2>& c, const float2* src, do
   const bool prof = c.prof_on && tid == 0;
   // TMEM columns: v_{k-1} of tile cc at tV + 16 cc, H v_{k-1} at tH + 16 cc, and H W_k of the
   // tile in hand at tP while the step's scalars are formed
-  const uint32_t tV = c.tm, tH = c.tm + 32u, tP = c.tm + 64u;
+  const uint32_t tV = c.tm, tH = c.tm + 32u, tP = c.tm + 64u, tW = c.tm + 96u;
   if (tid == 0) {
     ResCtx& r = ss.r;
     r.tbase[0] = c.tile_base(0);
@@ -1493,58 +1502,143 @@ __device__ __forceinline__ void stv4_hint(float4* p, float4 v, unsigned long lon
                : "memory");
 }
 
-// Cross-tile part of H W for one tile in the pair layout (table entries i0 .. i1), added to the
-// in-tile part parked in tensor memory at taddr, which is parked there again (the store is not
-// waited for): h[a] += wgt W[partner] for the own amplitude a = 2g + x at pair tid + 512 g.  A
-// whole-tile entry feeds every own pair, element for element; a half entry (the bond between the
-// top in-tile bit and the lowest tile bit) feeds the own half (bit 11 = bit 1 of g) from pairs
-// tid + 512 g' of the 1024-pair half block.  Three entries in flight; the parked part is loaded once
-// the first entries' loads are under way.  Earlier tensor-memory stores to taddr are waited for.
-__device__ __forceinline__ void partner_acc(const SmemSlice& ss, const float2* pv, int i0, int i1, uint32_t taddr) {
-  constexpr int G = 3;
-  const int tid = threadIdx.x;
-  const float hxy = ss.r.hxy, cu_sx = ss.r.cusx;
-  if (i0 >= i1) return;  // no block leaves this tile: the parked part is complete
-  float4 q[G][4];
-  float wq[G];
-  auto load = [&](int ib) {
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      const int i = ib + u;
-      const unsigned e = (i < i1) ? ss.ctab[i] : 0u;
-      // own pairs g fed by this entry: all four, or the half (g >> 1) == own half
-      const unsigned hm = (i >= i1) ? 0u : ((e & 4u) ? 0xfu : (((e >> 1) & 1u) ? 0xcu : 0x3u));
-      wq[u] = (e & 1u) ? cu_sx : hxy;
-      const float4* sb = reinterpret_cast<const float4*>(pv + ((size_t)(e >> 3) << 11)) + tid;
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        const int gs = (e & 4u) ? g : (g & 1);  // a half block holds pairs tid + 512 g' (g' = g & 1)
-        q[u][g] = ((hm >> g) & 1u) ? ldv4(sb + 512 * gs) : make_float4(0.f, 0.f, 0.f, 0.f);
+// Units of the partner ring (thread 0, once per slice, from the chunk table): a whole-tile entry
+// gives two units -- own pairs g = 0, 1 from granules 0, 1 of the block, g = 2, 3 from granules
+// 2, 3 -- and a half entry (bond 11) one: own half h, pairs g = 2h, 2h + 1, from granules 0, 1 of
+// the half block.  Granule g of a block is the float4 at 512 g + tid.  Unit word: bits 2.. = the
+// unit's first granule in float4 from the vector's start, bit 1 = the own half d (pairs 2d,
+// 2d + 1), bit 0 = weight of the Sx control instead of Jxy/2.  Tile 0's units (n_units0 of them)
+// come first, then tile 1's.
+__device__ __forceinline__ void build_unit_table(SmemSlice& ss, int n_own) {
+  int n = 0;
+  for (int cc = 0; cc < n_own; ++cc) {
+    for (int i = ss.ct_start[cc]; i < ss.ct_start[cc + 1]; ++i) {
+      const unsigned e = ss.ctab[i];
+      const unsigned off4 = (e >> 3) << 10;  // 2048 amplitudes = 1024 float4
+      if (e & 4u) {
+        ss.utab[n++] = (off4 << 2) | (e & 1u);
+        ss.utab[n++] = ((off4 + 1024u) << 2) | 2u | (e & 1u);
+      } else {
+        ss.utab[n++] = (off4 << 2) | (((e >> 1) & 1u) << 1) | (e & 1u);
       }
     }
-  };
-  load(i0);
-  float2 h[8];
-  tmem_st_wait();
-  tmem_ld8c(taddr, h);  // the parked in-tile part, while the first loads are in flight
-  for (int ib = i0;;) {
-#pragma unroll
-    for (int u = 0; u < G; ++u)
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        h[2 * g] = f2fma(f2(wq[u]), lo2(q[u][g]), h[2 * g]);
-        h[2 * g + 1] = f2fma(f2(wq[u]), hi2(q[u][g]), h[2 * g + 1]);
-      }
-    ib += G;
-    if (ib >= i1) break;
-    load(ib);
+    if (cc == 0) ss.n_units0 = n;
   }
-  tmem_st8c_nowait(taddr, h);
+  ss.n_units = n;
+}
+
+// h[4d .. 4d + 3] += wt (a, b): one unit's two granules added to own pairs 2d, 2d + 1.
+__device__ __forceinline__ void unit_acc(float2 (&h)[8], unsigned d, float wt, float4 a, float4 b) {
+  if (d == 0) {
+    h[0] = f2fma(f2(wt), lo2(a), h[0]);
+    h[1] = f2fma(f2(wt), hi2(a), h[1]);
+    h[2] = f2fma(f2(wt), lo2(b), h[2]);
+    h[3] = f2fma(f2(wt), hi2(b), h[3]);
+  } else {
+    h[4] = f2fma(f2(wt), lo2(a), h[4]);
+    h[5] = f2fma(f2(wt), hi2(a), h[5]);
+    h[6] = f2fma(f2(wt), lo2(b), h[6]);
+    h[7] = f2fma(f2(wt), hi2(b), h[7]);
+  }
+}
+
+// Partner ring of the headline loop.  The partner granules of W_k stream through this thread's
+// slots of a ring of kPrRing units in shared memory by 16-byte asynchronous copies (cp.async.cg:
+// L2 only; the blocks were written by other CTAs before the group barrier).  pring_start puts the
+// first kPrRing units in flight; pring_take adds units [u0, u1) to h in table order (h holds the
+// in-tile part of H W_k of the tile they feed), each unit taken freeing its slot for the unit
+// kPrRing further on.  A thread reads back only the granules it copied, so no block barrier is
+// needed, and no register holds a load in flight.
+__device__ __forceinline__ void pring_start(const SmemSlice& ss, const float2* pv) {
+  const int tid = threadIdx.x;
+  const int nU = ss.n_units;
+  const float4* v4 = reinterpret_cast<const float4*>(pv) + tid;
+  float4* slot0 = ss.r.pring + tid;
+#pragma unroll
+  for (int s = 0; s < kPrRing; ++s) {
+    if (s < nU) {
+      const float4* src = v4 + (ss.utab[s] >> 2);
+      cp_async16(slot0 + s * (2 * kThreads), src);
+      cp_async16(slot0 + s * (2 * kThreads) + kThreads, src + kThreads);
+    }
+    cp_async_commit();
+  }
+}
+__device__ __forceinline__ void pring_take(const SmemSlice& ss, const float2* pv, int u0, int u1, float2 (&h)[8]) {
+  constexpr int R = kPrRing;
+  const int tid = threadIdx.x;
+  const int nU = ss.n_units;
+  const float4* v4 = reinterpret_cast<const float4*>(pv) + tid;
+  float4* slot0 = ss.r.pring + tid;
+  const float hxy = ss.r.hxy, cu_sx = ss.r.cusx;
+  int s = u0 % R;  // unit u sits in slot u % R
+#pragma unroll 1
+  for (int u = u0; u < u1; ++u) {
+    cp_async_wait<R - 1>();  // this thread's granules of unit u have landed
+    const unsigned w = ss.utab[u];
+    float4* q = slot0 + s * (2 * kThreads);
+    const float4 a = q[0], b = q[kThreads];
+    unit_acc(h, (w >> 1) & 1u, (w & 1u) ? cu_sx : hxy, a, b);
+    if (u + R < nU) {
+      const float4* src = v4 + (ss.utab[u + R] >> 2);
+      cp_async16(q, src);
+      cp_async16(q + kThreads, src + kThreads);
+    }
+    cp_async_commit();
+    s = (s + 1 == R) ? 0 : s + 1;
+  }
+}
+
+// Step k's update of own tile cc from the complete H W_k parked in tensor memory (tP + 16 cc) and
+// the own W_k (tW + 16 cc): v_k, H v_k and W_{k+1} (tensor memory, not waited for), W_{k+1} = H v_k - b_k v_{k-1} (shared memory and basis slot k+1,
+// unless this is the slice's last step) and the tile's share of the step's partial sums.
+// It runs pair by pair (pair g: TMEM columns 4 g .. 4 g + 3 of each quantity).
+__device__ __forceinline__ void update_tile(const SmemSlice& ss, int cc, int k, uint32_t tP, uint32_t tV, uint32_t tH,
+                                            uint32_t tW, float2& acc_a, float2& acc_n, float2& acc_q) {
+  constexpr int T = 4096;
+  const int tid = threadIdx.x;
+  const bool last = (k == ss.r.m - 1);
+  const float ap = ss.f_ap, ib = ss.f_ib, bk = ss.f_bk;
+  float4* sw4 = reinterpret_cast<float4*>(ss.r.sw + cc * T);
+  float4* d4 = reinterpret_cast<float4*>(ss.r.basis + (size_t)k * ss.r.D + ss.r.tbase[cc]);  // W_{k+1}: slot k+1
+  const unsigned long long keep = l2_evict_last();
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {  // pair g: TMEM columns 4 g .. 4 g + 3
+    const uint32_t co = 16u * cc + 4u * g;
+    float2 hw[2], vp[2], hp[2], wo[2];
+    tmem_ld2c_x4(tP + co, tV + co, tH + co, tW + co, hw, vp, hp, wo);  // vp, hp unused at k = 0
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      float2 v, hv, w;
+      if (k == 0) {
+        v = f2mul(wo[a], f2(ib));
+        hv = f2mul(hw[a], f2(ib));
+        w = hv;
+      } else {
+        v = f2mul(f2fma(f2(-ap), vp[a], wo[a]), f2(ib));
+        hv = f2mul(f2fma(f2(-ap), hp[a], hw[a]), f2(ib));
+        w = f2fma(f2(-bk), vp[a], hv);
+      }
+      acc_a = f2fma(v, w, acc_a);
+      acc_n = f2fma(w, w, acc_n);
+      acc_q = f2fma(v, v, acc_q);
+      vp[a] = v;
+      hp[a] = hv;
+      wo[a] = w;
+    }
+    if (!last) {
+      tmem_st2c_x3_nowait(tV + co, tH + co, tW + co, vp, hp, wo);
+      const float4 w4 = pair4(wo[0], wo[1]);
+      sw4[tid + 512 * g] = w4;
+      stv4_hint(d4 + tid + 512 * g, w4, keep);
+    }
+  }
 }
 
 // In-tile part of H_j W for the own pairs of tile cc, from shared memory only: the bonds inside
 // the tile (times Jxy/2), the diagonal (formed once per slice) and an Sx control inside the tile;
-// parked in tensor memory at tP + 16 cc (the store is not waited for here).  Index bits of an
+// parked in tensor memory at tP + 16 cc (the store is not waited for here).  The thread's own pairs
+// come from tensor memory (tW + 16 cc), their neighbours' from shared memory.  Index bits of an
 // own amplitude: bit 0 = x, bits 1..9 = tid, bits 10, 11 = g.  Bonds:
 //   bond 0 (bits 0, 1): the element x = 1 - (tid & 1) of each pair, partner element tid & 1 of
 //     pair tid ^ 1;
@@ -1552,7 +1646,7 @@ __device__ __forceinline__ void partner_acc(const SmemSlice& ss, const float2* p
 //   bond 9 (tid bit 8, g bit 0): pair (tid ^ 256) + 512 (g ^ 1) where they differ;
 //   bond 10 (g bits 0, 1): own pair g ^ 3 for g = 1, 2 (registers).
 // An Sx control on site 1 (bit 0) couples the two elements of an own pair (registers).
-__device__ __forceinline__ void stencil_park(const SmemSlice& ss, int cc, uint32_t tP) {
+__device__ __forceinline__ void stencil_park(const SmemSlice& ss, int cc, uint32_t tP, uint32_t tW) {
   constexpr int T = 4096;
   const int tid = threadIdx.x;
   const float4* sw4 = reinterpret_cast<const float4*>(ss.r.sw + cc * T);
@@ -1598,8 +1692,12 @@ __device__ __forceinline__ void stencil_park(const SmemSlice& ss, int cc, uint32
   const int hs = ss.r.hs;
   const float2* dg = reinterpret_cast<const float2*>(ss.r.ring) + cc * (T / 2);
   float4 wp[4];
+  {  // the own pairs, from tensor memory (the caller has waited for their stores)
+    float2 w8[8];
+    tmem_ld8c(tW + 16u * cc, w8);
 #pragma unroll
-  for (int g = 0; g < 4; ++g) wp[g] = sw4[tid + 512 * g];
+    for (int g = 0; g < 4; ++g) wp[g] = pair4(w8[2 * g], w8[2 * g + 1]);
+  }
   // bond 10 (g bits 0, 1): g = 1 <-> g = 2
   h[2] = f2add(h[2], lo2(wp[2]));
   h[3] = f2add(h[3], hi2(wp[2]));
@@ -1662,18 +1760,21 @@ __device__ __noinline__ bool res64b_explicit_norm(SmemSlice& ss, uint32_t tV, in
 // Lanczos loop of one slice for complex64 tiles of 4096 amplitudes, two per CTA, resident: the
 // algebra and storage of lanczos_res64 (stencil on the raw vector W_k, H v_k by its two-term
 // recurrence, basis slots holding W_k, v_{k-1} and H v_{k-1} in tensor memory, W_k of the own
-// tiles in shared memory), in the pair layout -- thread tid owns the amplitude pairs
+// tiles in shared memory for the neighbours and in tensor memory for the owning thread), in the
+// pair layout -- thread tid owns the amplitude pairs
 // P = tid + 512 g (g < 4) of each own tile, amplitudes 2P and 2P + 1, so that every vector access
 // moves 16 bytes -- with group sums in fixed point, served by the block's control warp
 // (res64b_control).  Step k, for the 16 worker warps:
 //   1. (the in-tile part of H W_k is parked in tensor memory) wait until W_k is visible to the
 //      group (named barrier kBarGroup; nothing to wait for at k = 0);
 //   2. both tiles: H W_k = the parked in-tile part + the partner blocks of W_k from other tiles
-//      (plain L2 loads, two table entries in flight);
+//      (16-byte asynchronous copies through a per-thread ring in shared memory, kPrRing units
+//      of 16 KB per CTA in flight);
 //   3. take alpha_{k-1}, b_k and the scalars of step k, which the control warp formed from the
 //      group totals during stage 2 (named barrier kBarScal); b_k explicitly near an invariant
 //      subspace;
-//   4. both tiles: v_k, H v_k, W_{k+1} (shared memory and basis slot k+1), partial sums;
+//   4. both tiles: v_k, H v_k, W_{k+1} (tensor memory, shared memory and basis slot k+1), partial
+//      sums;
 //   5. hand the warps' partial sums to the control warp (named barrier kBarPost; no wait): it
 //      adds the CTA's share to the group sums and arrives at the group barrier, which waits
 //      for the W_{k+1} stores to drain;
@@ -1688,8 +1789,8 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
   const int tid = threadIdx.x;
   const bool prof = c.prof_on && tid == 0;
   // TMEM columns: v_{k-1} of tile cc at tV + 16 cc, H v_{k-1} at tH + 16 cc, the in-tile part
-  // of H W_k at tP + 16 cc
-  const uint32_t tV = c.tm, tH = c.tm + 32u, tP = c.tm + 64u;
+  // of H W_k at tP + 16 cc, the thread's own pairs of W_k at tW + 16 cc (all 128 columns)
+  const uint32_t tV = c.tm, tH = c.tm + 32u, tP = c.tm + 64u, tW = c.tm + 96u;
   if (tid == 0) {
     ResCtx& r = ss.r;
     r.tbase[0] = c.tile_base(0);
@@ -1698,6 +1799,7 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
     r.D = c.D;
     r.sw = c.sv[0];
     r.ring = c.sv[1];  // here: the diagonal of H_j, [2 tiles][2048 pairs] float2
+    r.pring = reinterpret_cast<float4*>(c.sv[1] + NB * (T / 2));  // partner ring behind it
     r.maskL1 = c.maskL1;
     r.mk = (unsigned)p.hc_mask;
     r.L1 = p.L - 1;
@@ -1727,6 +1829,7 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
     lz_init(ss, nrm_src, p.m);
     ss.ff_e_set = 0u;
     build_chunk_table(c, p, ss);
+    build_unit_table(ss, c.n_own);
   }
   // W_0 = psi: the own pairs into shared memory; the diagonal of H_j (pair order) beside it
   {
@@ -1741,9 +1844,14 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
       if (cc >= c.n_own) break;
       const size_t base = c.tile_base(cc);
       const float4* s4 = reinterpret_cast<const float4*>(src + base);
+      float2 w4[4];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        sw4[cc * (T / 2) + tid + 512 * g] = ldv4(s4 + tid + 512 * g);
+        const float4 q = ldv4(s4 + tid + 512 * g);
+        sw4[cc * (T / 2) + tid + 512 * g] = q;
+        w4[2 * (g & 1)] = lo2(q);
+        w4[2 * (g & 1) + 1] = hi2(q);
+        if (g & 1) tmem_st4c_nowait(tW + 16u * cc + 8u * (g >> 1), w4);  // own pairs of W_0 (update, stencil)
         float dd[2];
 #pragma unroll
         for (int x = 0; x < 2; ++x) {
@@ -1760,12 +1868,12 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
   if (ss.meff == 0) return true;
   const int m = ss.r.m;
   const int n_own = ss.r.n_own;
-  for (int cc = 0; cc < n_own; ++cc) stencil_park(ss, cc, tP);  // in-tile part of H W_0
+  tmem_st_wait();  // W_0's own pairs
+  for (int cc = 0; cc < n_own; ++cc) stencil_park(ss, cc, tP, tW);  // in-tile part of H W_0
   const float2* vec = src;  // W_k: the vector whose partner blocks are read in step k
   bool done = false;
   for (int k = 0; k < m; ++k) {
     const bool last = (k == m - 1);
-    float2* wdst = last ? nullptr : ss.r.basis + (size_t)k * ss.r.D;  // W_{k+1}: basis slot k+1
     // ---- 1. W_k is visible to the group (the barrier of step k - 1)
     if (k > 0) {
       nbar_sync(kBarGroup, kCtlThreads);
@@ -1776,9 +1884,23 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
       }
       if (prof) prof_mark(ss, 2);
     }
-    // ---- 2. H W_k of both tiles: the parked in-tile part plus the partner blocks, parked again
-#pragma unroll 1
-    for (int cc = 0; cc < n_own; ++cc) partner_acc(ss, vec, ss.ct_start[cc], ss.ct_start[cc + 1], tP + 16u * cc);
+    // ---- 2. H W_k of both tiles: the parked in-tile parts plus the partner blocks, which stream
+    // through the ring (tile 0's units first), parked again
+    {
+      pring_start(ss, vec);
+      float2 h[8];
+      tmem_st_wait();  // the in-tile parts were parked without a wait
+      tmem_ld8c(tP, h);
+      pring_take(ss, vec, 0, ss.n_units0, h);
+      if (n_own > 1) {
+        tmem_st8c_nowait(tP, h);
+        tmem_ld8c(tP + 16u, h);
+        pring_take(ss, vec, ss.n_units0, ss.n_units, h);
+        tmem_st8c_nowait(tP + 16u, h);
+      } else {
+        tmem_st8c_nowait(tP, h);
+      }
+    }
     if (prof) prof_mark(ss, 0);
     // ---- 3. alpha_{k-1}, b_k and the scalars of step k (formed by the control warp)
     if (k > 0) {
@@ -1798,57 +1920,9 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
     if (prof) prof_mark(ss, 3);
     // ---- 4. v_k, H v_k, W_{k+1} = H v_k - b_k v_{k-1} for the own amplitudes; partial sums
     float2 acc_a = f2(0.f), acc_n = f2(0.f), acc_q = f2(0.f);
-    {
-      const float ap = ss.f_ap, ib = ss.f_ib, bk = ss.f_bk;
-      tmem_st_wait();  // H W_k parked above
+    tmem_st_wait();  // H W_k parked above
 #pragma unroll 1
-      for (int cc = 0; cc < n_own; ++cc) {
-        float4* sw4 = reinterpret_cast<float4*>(ss.r.sw + cc * T);
-        float4* d4 = last ? nullptr : reinterpret_cast<float4*>(wdst + ss.r.tbase[cc]);
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {  // pairs g = 2 hf, 2 hf + 1: TMEM columns 8 hf .. 8 hf + 7
-          const uint32_t co = 16u * cc + 8u * hf;
-          float2 vp[4], hp[4], wo[4], hw[4];
-          tmem_ld4c_x3(tP + co, tV + co, tH + co, hw, vp, hp);  // vp, hp unused at k = 0
-#pragma unroll
-          for (int x = 0; x < 2; ++x) {
-            const float4 w4 = sw4[tid + 512 * (2 * hf + x)];
-            wo[2 * x] = lo2(w4);
-            wo[2 * x + 1] = hi2(w4);
-          }
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            float2 v, hv, w;
-            if (k == 0) {
-              v = f2mul(wo[a], f2(ib));
-              hv = f2mul(hw[a], f2(ib));
-              w = hv;
-            } else {
-              v = f2mul(f2fma(f2(-ap), vp[a], wo[a]), f2(ib));
-              hv = f2mul(f2fma(f2(-ap), hp[a], hw[a]), f2(ib));
-              w = f2fma(f2(-bk), vp[a], hv);
-            }
-            acc_a = f2fma(v, w, acc_a);
-            acc_n = f2fma(w, w, acc_n);
-            acc_q = f2fma(v, v, acc_q);
-            vp[a] = v;
-            hp[a] = hv;
-            wo[a] = w;
-          }
-          if (!last) {
-            tmem_st8x2_nowait(tV + co, tH + co, vp, hp);
-            const unsigned long long keep = l2_evict_last();
-#pragma unroll
-            for (int x = 0; x < 2; ++x) {
-              const int g = 2 * hf + x;
-              const float4 w4 = pair4(wo[2 * x], wo[2 * x + 1]);
-              sw4[tid + 512 * g] = w4;
-              stv4_hint(d4 + tid + 512 * g, w4, keep);
-            }
-          }
-        }
-      }
-    }
+    for (int cc = 0; cc < n_own; ++cc) update_tile(ss, cc, k, tP, tV, tH, tW, acc_a, acc_n, acc_q);
     if (prof) prof_mark(ss, 1);
     // ---- 5. the warps' partial sums of step k to the control warp (it arrives for the CTA)
     {
@@ -1864,9 +1938,10 @@ __device__ __noinline__ bool lanczos_res64b(Ctx<float2>& c, const float2* src, d
     // amplitudes of W_{k+1} in shared memory: one workers' barrier first)
     if (!last) {
       wsync();
-      for (int cc = 0; cc < n_own; ++cc) stencil_park(ss, cc, tP);
+      tmem_st_wait();  // W_{k+1}'s own pairs
+      for (int cc = 0; cc < n_own; ++cc) stencil_park(ss, cc, tP, tW);
     }
-    vec = wdst;
+    vec = ss.r.basis + (size_t)k * ss.r.D;  // W_{k+1}: basis slot k+1
     if (last) done = true;
   }
   tmem_st_wait();  // every store of v_k, H v_k has completed
@@ -2678,8 +2753,9 @@ template <class V, class A, int APT, int TPC, bool RES, int MODE>
 static KernelChoice choice(int t_bits) {
   constexpr int NB = RES ? TPC : 1;
   // complex64 streaming: two v_k tiles for the stencil plus the per-thread copy ring
-  const size_t smem = (MODE == kModeStream64) ? kStrSmemBytes
-                                              : (size_t)(RES ? 3 : 2) * NB * ((size_t)1 << t_bits) * sizeof(V);
+  const size_t smem = (MODE == kModeStream64)      ? kStrSmemBytes
+                      : (MODE == kModeResident64b) ? kRes64bSmemBytes
+                                                   : (size_t)(RES ? 3 : 2) * NB * ((size_t)1 << t_bits) * sizeof(V);
   return {(const void*)kg_eval_kernel<V, A, APT, TPC, RES, MODE>, smem, eval_threads(MODE)};
 }
 
