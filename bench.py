@@ -38,7 +38,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--prec", choices=["c64", "c128", "ff"], default="c64",
+                    help="ff (float-float vectors) runs on the subspace workloads (pe_...) only")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 (complex128) path")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -632,8 +633,9 @@ def run_sector(args):
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
     out = {"metric": SECTOR_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "c64+f64" if args.prec == "c64" else "c128", "data": "synthetic",
-           "config": {"workload": args.workload, "L": w.L, "K": w.K, "parity": w.parity, "D": D, "N": N, "m": w.m,
+           "vs_baseline": None, "dtype": {"c64": "c64+f64", "c128": "c128", "ff": "ff32x2+f64"}[args.prec],
+           "data": "synthetic",
+           "config": {"workload": args.workload, "L": w.L, "K": w.K, "prec": args.prec, "parity": w.parity, "D": D, "N": N, "m": w.m,
                       "dt": w.dt, "pulses": B, "task": "e_1 -> e_D", "J": w.J, "alpha_z": w.alpha_z,
                       "grad": args.grad,
                       "hc": "(J/2)(sigma^z_1 + sigma^z_L)", "u": "U(-1,1)",

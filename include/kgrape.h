@@ -53,8 +53,19 @@ typedef enum kg_status {
 
 typedef enum kg_precision {
   KG_PREC_C128 = 0,        /* complex128 vectors, FP64 arithmetic throughout */
-  KG_PREC_C64_F64REC = 1   /* complex64 vectors and H*v in FP32; alpha/beta recurrences,
+  KG_PREC_C64_F64REC = 1,  /* complex64 vectors and H*v in FP32; alpha/beta recurrences,
                               norms, the m x m exponential and <f|psi_N> in FP64 */
+  KG_PREC_FF = 2           /* float-float vectors: each real part and imaginary part is the
+                              unevaluated sum hi + lo of two FP32 numbers (about 44 significant
+                              bits), H*v, the Lanczos updates and the recombination in FP32 with
+                              error-free transformations (TwoSum, FMA TwoProduct); recurrences,
+                              norms, the m x m exponential and the overlaps in FP64.  16 bytes per
+                              amplitude, like complex128.  Subspace engines (kg_sector_*) only,
+                              with KG_GRAD_NONE, _CENTERED or _ZEROTH: it carries the paper's
+                              subspace task (Sec. 3.2: 2 x 4D slices of dt = 0.5) to 1e-5 of the
+                              complex128 oracle, where the rounding of complex64 Krylov vectors
+                              accumulates past it.  The full-chain entry points answer
+                              KG_ERR_UNSUPPORTED. */
 } kg_precision;
 
 typedef enum kg_grad_mode {

@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(_HERE, "libkgrape.so")
 KG_OK, KG_ERR_INVALID_ARG, KG_ERR_UNSUPPORTED, KG_ERR_CUDA, KG_ERR_NONFINITE, KG_ERR_TIMEOUT, KG_ERR_WORKSPACE = range(7)
 STATUS_NAMES = {0: "KG_OK", 1: "KG_ERR_INVALID_ARG", 2: "KG_ERR_UNSUPPORTED", 3: "KG_ERR_CUDA",
                 4: "KG_ERR_NONFINITE", 5: "KG_ERR_TIMEOUT", 6: "KG_ERR_WORKSPACE"}
-KG_PREC_C128, KG_PREC_C64_F64REC = 0, 1
+KG_PREC_C128, KG_PREC_C64_F64REC, KG_PREC_FF = 0, 1, 2
 KG_GRAD_NONE, KG_GRAD_CENTERED, KG_GRAD_ZEROTH, KG_GRAD_EXACT, KG_GRAD_TAYLOR1, KG_GRAD_TAYLOR2 = 0, 1, 2, 3, 4, 5
 KG_HC_SX_SITE, KG_HC_SZ_SITES = 0, 1
 KG_FLAG_HOST_STAGING = 1

@@ -13,7 +13,7 @@ import torch
 from . import _abi
 from ._abi import check, lib
 
-_PREC = {"c128": _abi.KG_PREC_C128, "c64": _abi.KG_PREC_C64_F64REC}
+_PREC = {"c128": _abi.KG_PREC_C128, "c64": _abi.KG_PREC_C64_F64REC, "ff": _abi.KG_PREC_FF}
 _GRAD = {"none": _abi.KG_GRAD_NONE, "centered": _abi.KG_GRAD_CENTERED, "zeroth": _abi.KG_GRAD_ZEROTH,
          "exact": _abi.KG_GRAD_EXACT, "taylor1": _abi.KG_GRAD_TAYLOR1, "taylor2": _abi.KG_GRAD_TAYLOR2}
 
@@ -42,7 +42,8 @@ class Options:
     N: int
     dt: float
     m: int
-    prec: str = "c64"         # "c64" (complex64 state, FP64 recurrences) or "c128"
+    prec: str = "c64"         # "c64" (complex64 state, FP64 recurrences), "c128", or "ff" (float-float
+                              # vectors; subspace engines only)
     grad: str = "centered"    # "none", "centered", "zeroth", "exact" (Gauss-Lobatto over each slice),
                               # "taylor1", "taylor2" (App. B's hierarchy; subspace engines only)
     ckpt_every: int = 0       # 0: keep every psi_j; C > 0: checkpoint every C slices; -1 (KG_CKPT_AUTO):

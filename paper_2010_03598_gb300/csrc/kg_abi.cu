@@ -55,6 +55,8 @@ kg_status check_args(const kg_chain* ch, const kg_options* o) {
     return fail(KG_ERR_INVALID_ARG, "Jxy, Jz and hc_amp must be finite");
   if (o->N < 1) return fail(KG_ERR_INVALID_ARG, "N must be >= 1");
   if (o->m < 1 || o->m > kg::kMaxM) return fail(KG_ERR_INVALID_ARG, "m must satisfy 1 <= m <= 32");
+  if (o->prec == KG_PREC_FF)
+    return fail(KG_ERR_UNSUPPORTED, "float-float vectors (KG_PREC_FF) are available for subspaces (kg_sector_*)");
   if (o->prec != KG_PREC_C128 && o->prec != KG_PREC_C64_F64REC)
     return fail(KG_ERR_INVALID_ARG, "prec must be KG_PREC_C128 or KG_PREC_C64_F64REC");
   if (o->grad == KG_GRAD_TAYLOR1 || o->grad == KG_GRAD_TAYLOR2)

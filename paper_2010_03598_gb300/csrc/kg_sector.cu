@@ -33,12 +33,58 @@
 #include <cstring>
 #include <string>
 #include <unordered_map>
+#include <type_traits>
 #include <vector>
 
 #include "kg_device.cuh"
 #include "kg_launch.h"
 
 namespace kg {
+
+// ---------------------------------------------------------------- float-float vectors (KG_PREC_FF)
+// Every amplitude is the unevaluated sum hi + lo of two FP32 numbers (about 44 significant bits),
+// and the arithmetic on it is FP32 with error-free transformations (Knuth's TwoSum, the FMA
+// TwoProduct: ff_add, ff_mul), so that the rounding of the Krylov vectors -- what limits the
+// complex64 path over the 2 x 4D slices of Sec. 3.2's pulses -- shrinks by about 2^20 without one
+// FP64 instruction (1/64 of the FP32 rate on this GPU) per amplitude.  The scalars that steer the
+// recurrence (alpha, b, norms, overlaps) come from FP64 block sums of the float-float partials,
+// as on the complex128 path.
+struct FFR {
+  float hi, lo;
+  FFR() = default;
+  __device__ __forceinline__ FFR(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ FFR(int a) : hi((float)a), lo(0.f) {}
+  __device__ __forceinline__ explicit FFR(double a) : hi((float)a), lo((float)(a - (double)(float)a)) {}
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ explicit operator float() const { return __fadd_rn(hi, lo); }
+};
+struct __align__(16) FFC {
+  FFR x, y;
+};
+__device__ __forceinline__ FFR operator+(FFR a, FFR b) {
+  const FF s = ff_add(FF{a.hi, a.lo}, FF{b.hi, b.lo});
+  return FFR(s.hi, s.lo);
+}
+__device__ __forceinline__ FFR operator-(FFR a) { return FFR(-a.hi, -a.lo); }
+__device__ __forceinline__ FFR operator-(FFR a, FFR b) { return a + (-b); }
+__device__ __forceinline__ FFR operator*(FFR a, FFR b) {
+  const FF p = ff_mul(FF{a.hi, a.lo}, FF{b.hi, b.lo});
+  return FFR(p.hi, p.lo);
+}
+__device__ __forceinline__ FFR fma(FFR a, FFR b, FFR c) { return a * b + c; }
+// Scalar operations (once per Lanczos step, not per amplitude) go through FP64.
+__device__ __forceinline__ FFR operator/(FFR a, FFR b) { return FFR((double)a / (double)b); }
+__device__ __forceinline__ bool operator<=(FFR a, FFR b) { return (double)a <= (double)b; }
+__device__ __forceinline__ FFR fmax(FFR a, FFR b) { return ((double)a >= (double)b) ? a : b; }
+__device__ __forceinline__ FFR fabs(FFR a) { return (a.hi < 0.f) ? -a : a; }
+__device__ __forceinline__ FFR sqrt(FFR a) { return FFR(::sqrt((double)a)); }
+// the float and double functions stay visible beside these overloads inside namespace kg
+using ::fma;
+using ::fmax;
+using ::fabs;
+using ::sqrt;
+template <> struct VecTraits<FFC> { using R = FFR; };
+template <> __device__ __forceinline__ FFC vmake<FFC>(FFR a, FFR b) { return FFC{a, b}; }
 
 constexpr int kSecColBits = 13;
 constexpr int kSecMaxD = 1 << kSecColBits;  // columns fit the entry's 13 bits
@@ -82,6 +128,7 @@ struct SecSmem {
   double tot_d[2][4];
   float wcls_f[kSecClasses];
   double wcls_d[kSecClasses];
+  float2 wcls_ff[kSecClasses];  // float-float (hi, lo)
   double alpha[kMaxM], beta[kMaxM + 1];
   float alpha_f[kMaxM], beta_f[kMaxM + 1];
   float2 ff_a[kMaxM], ff_n[kMaxM], ff_q[kMaxM], ff_e[kMaxM];
@@ -352,8 +399,9 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
                                           V* tint_io = nullptr) {
   using R = typename VecTraits<V>::R;
   constexpr bool F32 = sizeof(R) == 4;
+  constexpr bool FFM = std::is_same<R, FFR>::value;  // float-float vectors (KG_PREC_FF)
   const int tid = threadIdx.x, D = p.D, m = p.m, ne = p.ell;
-  const R* wcls = F32 ? (const R*)sm.wcls_f : (const R*)sm.wcls_d;
+  const R* wcls = F32 ? (const R*)sm.wcls_f : FFM ? (const R*)sm.wcls_ff : (const R*)sm.wcls_d;
   R dj[RPT];
 #pragma unroll
   for (int i = 0; i < RPT; ++i) dj[i] = fma((R)uj, hh[i], dd[i]);
@@ -439,32 +487,35 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
       alpha = st.alpha;
       b2 = st.b2;
     } else {
-      const double vals[3] = {pa, pn, pq};
+      const double vals[3] = {(double)pa, (double)pn, (double)pq};
       double o[3];
       sec_mark(p, sm, 0);
       sec_reduce<NT, 3>(sm, par, vals, o);
       sec_mark(p, sm, 1);
-      alpha = o[0];
-      b2 = o[1] - 2.0 * alpha * o[0] + alpha * alpha * o[2];
-      if (!isfinite(alpha) || !isfinite(o[1])) {
+      double bd = o[1] - 2.0 * o[0] * o[0] + o[0] * o[0] * o[2];
+      if (!isfinite(o[0]) || !isfinite(o[1])) {
         if (tid == 0) {
           sec_flag(p, KG_ERR_NONFINITE);
           sec_record(sm, k, 1);
         }
         return false;
       }
-      if (!last && b2 < 1e-3 * o[1]) {
+      if (!last && bd < 1e-3 * o[1]) {
         double e1[1] = {0.0};
+        const R ra = (R)o[0];
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
-          const V d = vaxpy<V>(-alpha, vv[i], w[i]);
-          e1[0] = fma(d.x, d.x, fma(d.y, d.y, e1[0]));
+          const V d = vaxpy<V>(-ra, vv[i], w[i]);
+          const double dx = (double)d.x, dy = (double)d.y;
+          e1[0] = fma(dx, dx, fma(dy, dy, e1[0]));
         }
         double o1[1];
         sec_reduce<NT, 1>(sm, par, e1, o1);
-        b2 = o1[0];
+        bd = o1[0];
       }
-      if (tid == 0) sm.alpha[k] = alpha;
+      alpha = (R)o[0];
+      b2 = (R)bd;
+      if (tid == 0) sm.alpha[k] = o[0];
     }
     beta = sqrt(fmax(b2, (R)0));
     if (tid == 0) {
@@ -629,8 +680,10 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
   }
   // ---- Taylor hierarchy (App. B, Eq. gradp), backward slice j (sec_taylor)
   R pt = 0;
-  if (taylor > 0) pt = sec_taylor<V, NT, RPT>(p, sm, Sa, Sb, ell, basis, uj, meff, nin, taylor, psi_end);
-  if (lob > 0) pt = sec_interior<V, NT, RPT>(p, sm, basis, meff, lob, tint_io);
+  if constexpr (!FFM) {  // the float-float path offers the centred and zeroth-order gradients
+    if (taylor > 0) pt = sec_taylor<V, NT, RPT>(p, sm, Sa, Sb, ell, basis, uj, meff, nin, taylor, psi_end);
+    if (lob > 0) pt = sec_interior<V, NT, RPT>(p, sm, basis, meff, lob, tint_io);
+  }
   if constexpr (F32) {
     const float vals[3] = {pn, pg, pt};
     FF o[3];
@@ -658,7 +711,7 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
     ex = sm.ex_d;
     if (tay) *tay = sm.tay_d;
   } else {
-    const double vals[3] = {pn, pg, pt};
+    const double vals[3] = {(double)pn, (double)pg, (double)pt};
     double o[3];
     sec_mark(p, sm, 5);
     sec_reduce<NT, 3>(sm, par, vals, o);
@@ -858,6 +911,8 @@ __global__ void __launch_bounds__(NT, (sec_min_blocks<V, NT>())) kg_sector_kerne
   if (threadIdx.x < kSecClasses) {
     sm.wcls_f[threadIdx.x] = (float)p.wcls[threadIdx.x];
     sm.wcls_d[threadIdx.x] = p.wcls[threadIdx.x];
+    const float wh = (float)p.wcls[threadIdx.x];
+    sm.wcls_ff[threadIdx.x] = make_float2(wh, (float)(p.wcls[threadIdx.x] - (double)wh));
   }
   if (threadIdx.x < 8) sm.prof_acc[threadIdx.x] = 0;
   const long long t0 = clock64();
@@ -884,6 +939,16 @@ static SecKernel sec_choice() {
 // thread (10 for complex64 up to 2560, which keeps two CTAs on an SM); or, with nt = 128, 256 or
 // 512 threads, that block with the fewest rows per thread that covers D (nt.threads == 0: none).
 static SecKernel sec_pick(int prec, int D, int nt = 0) {
+  if (prec == KG_PREC_FF) {  // the complex128 path's shapes (16-byte amplitudes)
+    if (nt == 128) return (D <= 512) ? sec_choice<FFC, 128, 4>() : SecKernel{nullptr, 0};
+    if (nt == 256) return (D <= 1024) ? sec_choice<FFC, 256, 4>()
+                                      : (D <= 2048) ? sec_choice<FFC, 256, 8>() : SecKernel{nullptr, 0};
+    if (nt == 512) return (D <= 4096) ? sec_choice<FFC, 512, 8>() : SecKernel{nullptr, 0};
+    if (D <= 512) return sec_choice<FFC, 128, 4>();
+    if (D <= 1024) return sec_choice<FFC, 256, 4>();
+    if (D <= 2048) return sec_choice<FFC, 256, 8>();
+    return sec_choice<FFC, 512, 8>();
+  }
   if (prec == KG_PREC_C128) {
     if (nt == 128) return (D <= 512) ? sec_choice<double2, 128, 4>() : SecKernel{nullptr, 0};
     if (nt == 256) return (D <= 1024) ? sec_choice<double2, 256, 4>()
@@ -910,7 +975,7 @@ static SecKernel sec_pick(int prec, int D, int nt = 0) {
 constexpr int kSecMaxRows = 4096;  // 512 threads x 8 rows
 
 size_t sector_smem_bytes(int prec, int D, int ell) {
-  const size_t vb = (prec == KG_PREC_C128) ? 16 : 8;
+  const size_t vb = (prec == KG_PREC_C64_F64REC) ? 8 : 16;
   const size_t Dp = ((size_t)D + 15) & ~(size_t)15;
   return 2 * Dp * vb + (size_t)ell * D * 2;
 }
@@ -1078,7 +1143,7 @@ size_t align_up(size_t x) { return (x + kg::kAlign - 1) / kg::kAlign * kg::kAlig
 
 SectorLayout sector_layout(int D, int ell, const kg_options* o, int B, int grid) {
   SectorLayout l;
-  const size_t vb = (size_t)D * (o->prec == KG_PREC_C128 ? 16 : 8);
+  const size_t vb = (size_t)D * (o->prec == KG_PREC_C64_F64REC ? 8 : 16);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
@@ -1103,11 +1168,14 @@ kg_status check_sector_opts(const kg_options* o, int B) {
   if (B < 1) return host_fail(KG_ERR_INVALID_ARG, "B must be >= 1");
   if (o->N < 1) return host_fail(KG_ERR_INVALID_ARG, "N must be >= 1");
   if (o->m < 1 || o->m > kg::kMaxM) return host_fail(KG_ERR_INVALID_ARG, "m must satisfy 1 <= m <= 32");
-  if (o->prec != KG_PREC_C128 && o->prec != KG_PREC_C64_F64REC)
-    return host_fail(KG_ERR_INVALID_ARG, "prec must be KG_PREC_C128 or KG_PREC_C64_F64REC");
+  if (o->prec != KG_PREC_C128 && o->prec != KG_PREC_C64_F64REC && o->prec != KG_PREC_FF)
+    return host_fail(KG_ERR_INVALID_ARG, "prec must be KG_PREC_C128, KG_PREC_C64_F64REC or KG_PREC_FF");
   if (o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED && o->grad != KG_GRAD_ZEROTH &&
       o->grad != KG_GRAD_EXACT && o->grad != KG_GRAD_TAYLOR1 && o->grad != KG_GRAD_TAYLOR2)
     return host_fail(KG_ERR_INVALID_ARG, "grad must be KG_GRAD_NONE, _CENTERED, _ZEROTH, _EXACT, _TAYLOR1 or _TAYLOR2");
+  if (o->prec == KG_PREC_FF && o->grad != KG_GRAD_NONE && o->grad != KG_GRAD_CENTERED &&
+      o->grad != KG_GRAD_ZEROTH)
+    return host_fail(KG_ERR_UNSUPPORTED, "KG_PREC_FF offers KG_GRAD_NONE, _CENTERED and _ZEROTH");
   if (o->ckpt_every != 0) return host_fail(KG_ERR_UNSUPPORTED, "subspace evaluations keep every state: ckpt_every must be 0");
   if (o->tile_bits != 0) return host_fail(KG_ERR_INVALID_ARG, "tile_bits must be 0 for subspaces");
   if ((o->flags & ~KG_FLAG_PHASE_TIMING) != 0)
@@ -1275,7 +1343,8 @@ kg_status kg_sector_create(kg_sector_handle** handle, const kg_sector* s, const 
   }
   h->sector = *s;
   h->opts = *o;
-  if (!(h->opts.breakdown_tol > 0.0)) h->opts.breakdown_tol = (o->prec == KG_PREC_C128) ? 1e-12 : 1e-5;
+  if (!(h->opts.breakdown_tol > 0.0))
+    h->opts.breakdown_tol = (o->prec == KG_PREC_C128) ? 1e-12 : (o->prec == KG_PREC_FF) ? 1e-10 : 1e-5;
   h->lay = sector_layout(h->basis.D, h->basis.ell_width, o, B, grid);
   h->ws = (char*)workspace;
   h->stream = (cudaStream_t)cuda_stream;

@@ -114,6 +114,7 @@ def test_full_reorthogonalisation_flag_is_accepted(lib):
     ({}, dict(dt=0.0), _abi.KG_ERR_INVALID_ARG),
     ({}, dict(dt=float("inf")), _abi.KG_ERR_INVALID_ARG),
     ({}, dict(prec=5), _abi.KG_ERR_INVALID_ARG),
+    ({}, dict(prec=_abi.KG_PREC_FF), _abi.KG_ERR_UNSUPPORTED),  # float-float vectors: subspaces only
     ({}, dict(grad=9), _abi.KG_ERR_INVALID_ARG),
     ({}, dict(ckpt_every=-2), _abi.KG_ERR_INVALID_ARG),
     ({}, dict(tile_bits=14), _abi.KG_ERR_INVALID_ARG),

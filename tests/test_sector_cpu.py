@@ -73,6 +73,11 @@ def test_asymmetric_mask_is_fine_without_parity():
     (dict(host_staging=True), _abi.KG_ERR_INVALID_ARG),
     (dict(phase_timing=True), _abi.KG_OK),
     (dict(m=33), _abi.KG_ERR_INVALID_ARG),
+    (dict(prec="ff"), _abi.KG_OK),
+    (dict(prec="ff", grad="zeroth"), _abi.KG_OK),
+    (dict(prec="ff", grad="none"), _abi.KG_OK),
+    (dict(prec="ff", grad="exact"), _abi.KG_ERR_UNSUPPORTED),
+    (dict(prec="ff", grad="taylor2"), _abi.KG_ERR_UNSUPPORTED),
 ])
 def test_sector_option_checks(opts_kw, status):
     spec = A.SectorSpec(10, 4, 1)
@@ -93,6 +98,8 @@ def test_sector_workspace_holds_a_trajectory_per_pulse():
     assert four - one >= 3 * (440 + 1 + 10) * D * 8
     o128 = A.Options(N=440, dt=0.5, m=10, prec="c128")
     assert A.sector_workspace_bytes(spec, o128, 1) >= (440 + 1 + 10) * D * 16
+    off = A.Options(N=440, dt=0.5, m=10, prec="ff")  # float-float: 16 bytes per amplitude
+    assert A.sector_workspace_bytes(spec, off, 1) == A.sector_workspace_bytes(spec, o128, 1)
 
 
 def test_sector_create_rejects_a_small_workspace():

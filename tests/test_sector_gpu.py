@@ -1,7 +1,7 @@
 """GPU parity of the parity-excitation subspace kernel (Sec. 3.1) against the oracle's reduction.
 
 Same tolerances as the full chain: complex128 |dF|/F, ||dg||/||g|| <= 1e-10; complex64 + FP64
-recurrences 1e-5 / 1e-4.  The cases cover every block shape of the kernel (128 x 4, 256 x 4,
+recurrences 1e-5 / 1e-4; float-float vectors (KG_PREC_FF) 1e-8 / 1e-7.  The cases cover every block shape of the kernel (128 x 4, 256 x 4,
 256 x 8 and 512 x 8 rows), both parities and the whole sector, the three gradient modes, Lanczos
 breakdowns (D < m, D = 1), a batch larger than the grid, and the paper's L = 20, K = 4 subspace.
 """
@@ -15,7 +15,7 @@ from paper_2010_03598_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"c128": (1e-10, 1e-10), "c64": (1e-5, 1e-4)}
+TOL = {"c128": (1e-10, 1e-10), "c64": (1e-5, 1e-4), "ff": (1e-8, 1e-7)}
 
 
 def api():
@@ -77,6 +77,11 @@ def problem(L, K, parity, N, seed, target="last"):
     (20, 4, 1, 24, "centered", "c64", "last"),     # D = 2445: 512 x 8
     (20, 4, 1, 12, "centered", "c128", "random"),
     (12, 6, -1, 40, "none", "c64", "random"),
+    (10, 4, 1, 440, "centered", "ff", "last"),    # float-float vectors: 128 x 4
+    (13, 6, 1, 50, "zeroth", "ff", "random"),     # 256 x 4
+    (17, 4, 1, 30, "centered", "ff", "random"),   # 256 x 8
+    (20, 4, 1, 12, "centered", "ff", "random"),   # 512 x 8
+    (12, 6, -1, 40, "none", "ff", "random"),
 ])
 def test_sector_vs_oracle(L, K, parity, N, grad, prec, target):
     A = api()
@@ -92,11 +97,11 @@ def test_sector_vs_oracle(L, K, parity, N, grad, prec, target):
         assert nrel(g[0], g_ref) <= tg, nrel(g[0], g_ref)
     assert rep["breakdowns"] == 0
     # ||psi_N||: FP32 rounding of the complex64 states walks by ~6e-8 per slice (sqrt(N) of it, x4 margin)
-    ntol = 1e-12 if prec == "c128" else 4 * 6e-8 * np.sqrt(N) + 1e-7
+    ntol = {"c128": 1e-12, "ff": 1e-10}.get(prec, 4 * 6e-8 * np.sqrt(N) + 1e-7)
     assert abs(rep["norm_final"] - np.linalg.norm(d["psi_N"])) <= ntol
 
 
-@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("prec", ["c128", "c64", "ff"])
 def test_sector_batch_larger_than_the_grid(prec):
     # 5 pulses on 2 CTAs: CTA b takes pulses b, b + 2, b + 4 in turn, reusing its trajectory buffer
     A = api()
@@ -117,7 +122,7 @@ def test_sector_batch_larger_than_the_grid(prec):
         assert nrel(g[b], g_ref) <= tg
 
 
-@pytest.mark.parametrize("L,K,prec", [(3, 1, "c128"), (4, 2, "c64"), (6, 0, "c128")])
+@pytest.mark.parametrize("L,K,prec", [(3, 1, "c128"), (4, 2, "c64"), (6, 0, "c128"), (4, 2, "ff")])
 def test_sector_breakdowns_match_the_oracle(L, K, prec):
     # D = 2, 4, 1 < m: every slice's Lanczos basis ends early at an invariant subspace
     A = api()
@@ -151,18 +156,37 @@ def test_sector_equals_the_full_chain_kernel():
     eng.close()
 
 
-def test_papers_workload_at_full_size():
-    # pe_L20_K4 at its full N = 4D = 9780 slices: F and the whole gradient against the oracle
-    # (complex128 oracle, one pulse; complex64 kernel, the benchmark's block shape)
-    A = api()
+@pytest.fixture(scope="module")
+def papers_workload_reference():
+    # pe_L20_K4 at its full N = 4D = 9780 slices, one pulse: the complex128 oracle's F and gradient
     w = W.SECTOR_WORKLOADS["pe_L20_K4"]
     c = S.paper_chain(w.L, w.K)
     U, psi0, f = W.sector_instance(w, c.D, batch=1)
     F_ref, g_ref, _ = oracle.evaluate(c, U[0], w.dt, w.m, psi0, f, "centered")
+    return w, U, psi0, f, F_ref, g_ref
+
+
+def test_papers_workload_at_full_size_float_float(papers_workload_reference):
+    # Sec. 3.2's task at full length within the reduced-precision tolerances (1e-5 on F, 1e-4 on the
+    # gradient): the float-float vectors keep the rounding of the 2 x 9780 slices' Krylov vectors
+    # far below them (F D = 0.34 for this pulse, so the relative F bound is the plain one)
+    A = api()
+    w, U, psi0, f, F_ref, g_ref = papers_workload_reference
+    fid, g, rep = run(A.SectorSpec(w.L, w.K, w.parity), A.Options(U.shape[1], w.dt, w.m, prec="ff"), U, psi0, f)
+    print("pe_L20_K4 full size, float-float: rel. err F", abs(fid[0] - F_ref) / F_ref, "grad", nrel(g[0], g_ref))
+    assert abs(fid[0] - F_ref) / F_ref <= 1e-5
+    assert nrel(g[0], g_ref) <= 1e-4
+
+
+def test_papers_workload_at_full_size_complex64(papers_workload_reference):
+    # the same pulse on complex64 vectors: the FP32 rounding of the Krylov vectors walks over the
+    # 2 x 9780 slices to a measured 7e-5 on F and 4.9e-5 on the gradient; held to 1e-4 / 1e-4
+    A = api()
+    w, U, psi0, f, F_ref, g_ref = papers_workload_reference
     fid, g, rep = run(A.SectorSpec(w.L, w.K, w.parity), A.Options(U.shape[1], w.dt, w.m, prec="c64"), U, psi0, f)
-    print("pe_L20_K4 full size: rel. err F", abs(fid[0] - F_ref) / F_ref, "grad", nrel(g[0], g_ref))
+    print("pe_L20_K4 full size, complex64: rel. err F", abs(fid[0] - F_ref) / F_ref, "grad", nrel(g[0], g_ref))
     assert abs(fid[0] - F_ref) / F_ref <= 1e-4
-    assert nrel(g[0], g_ref) <= 1e-3
+    assert nrel(g[0], g_ref) <= 1e-4
 
 
 @pytest.mark.parametrize("L,K,parity,N,grad,prec", [
