@@ -50,9 +50,13 @@ constexpr int kLzMaxChunks = 2 * (1 + (kMaxL - 13) + 1);  // two tiles: bond 11,
 // Headline loop (lanczos_res64b): partner blocks stream through a per-thread ring of kPrRing units
 // in the shared memory behind W_k (64 KB) and the diagonal (32 KB); a unit is two 16-byte granules
 // per thread, 16 KB per CTA.  A whole-tile table entry is two units, a half entry one.
-constexpr int kPrRing = 7;
+constexpr int kPrRing = 5;
 constexpr int kLzMaxUnits = 2 * kLzMaxChunks;
-constexpr size_t kRes64bSmemBytes = (size_t)96 * 1024 + (size_t)kPrRing * 16 * 1024;
+// Dynamic shared memory of the headline kernel: the Lanczos loop's W_k, diagonal and partner ring,
+// or the recombination's kRecombDepth (3) basis vectors of 64 KB, whichever is larger.
+constexpr size_t kRes64bSmemBytes = ((size_t)96 + (size_t)kPrRing * 16 > (size_t)3 * 64)
+                                        ? ((size_t)96 + (size_t)kPrRing * 16) * 1024
+                                        : (size_t)3 * 64 * 1024;
 constexpr uint32_t kTmemCols = 512;  // 128 columns per warp, 4 warps per lane quarter
 // Headline loop (lanczos_res64b): 16 worker warps and the control warp (warp 16), which meet at
 // named barriers -- kBarPost (workers arrive with a step's partial sums, the control warp waits),
