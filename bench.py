@@ -50,6 +50,8 @@ def parse_args():
                     help="gradient mode of the timed evaluations (the headline is the centred gradient; "
                          "taylor1/2 on subspace workloads only)")
     ap.add_argument("--reorth", action="store_true", help="full re-orthogonalisation of every Lanczos step")
+    ap.add_argument("--phases", action="store_true",
+                    help="print the headline loop's phase times (KG_FLAG_PHASE_TIMING, CTA 0) instead of a bench line")
     ap.add_argument("--batch", type=int, default=0,
                     help="pulses of a subspace workload (0: one per resident CTA of the subspace kernel)")
     return ap.parse_args()
@@ -653,8 +655,46 @@ def run_sector(args):
     eng.close()
 
 
+def run_phases(args):
+    """Phase times of the complex64 evaluation (clock64 marks of CTA 0's thread 0, KG_FLAG_PHASE_TIMING):
+    per Lanczos step and per slice, in microseconds at the SM clock read from nvidia-smi (2070 MHz if
+    unavailable).  A diagnostic: the marks add a little time, and the numbers are not a bench value."""
+    import torch
+
+    sys.path.insert(0, ROOT)
+    from paper_2010_03598_gb300 import api as A
+    W, w = workload(args.workload, args.N or 20)
+    dev = torch.device("cuda", 0)
+    u, psi0, f = W.instance(w)
+    eng = A.KGrape(A.ChainSpec(w.L, w.Jxy, w.Jz), A.Options(w.N, w.dt, w.m, prec="c64", phase_timing=True),
+                   device=dev)
+    ut, pt, ft = (torch.tensor(x, device=dev) for x in (u, psi0, f))
+    for _ in range(2):
+        eng.evaluate(ut, pt, ft)
+    pc = eng.sync()["phase_cycles"]
+    eng.close()
+    mhz = 2070.0
+    try:
+        r = subprocess.run(["nvidia-smi", "--query-gpu=clocks.sm", "--format=csv,noheader,nounits", "-i", "0"],
+                           capture_output=True, text=True, timeout=20)
+        mhz = float(r.stdout.strip().splitlines()[0]) or mhz
+    except Exception:
+        pass
+    us = [c / mhz for c in pc]
+    steps, slices = 2 * w.N * w.m, 2 * w.N
+    print(json.dumps({"workload": args.workload, "N": w.N, "sm_mhz": mhz, "total_us": us[7],
+                      "per_step_us": {"partner blocks": us[0] / steps, "update": us[1] / steps,
+                                      "hand-over, stencil, group wait": us[2] / steps,
+                                      "wait for the scalars": us[3] / steps},
+                      "per_slice_us": {"last barrier, T, exponential, coefficients": us[4] / slices,
+                                       "recombination, store, end-of-slice reduction": us[5] / slices}}))
+
+
 def main():
     args = parse_args()
+    if args.phases:
+        run_phases(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == BATCH_WORKLOAD:
