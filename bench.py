@@ -136,6 +136,51 @@ def err_vs_oracle(args, w, F, grad):
     return out
 
 
+def short_pulse_golden(workload_name: str, grad: str):
+    """A committed oracle golden of this workload on a shorter pulse (tests/golden), or None."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "oracle_*.json"))):
+        try:
+            with open(path) as fh:
+                gd = json.load(fh)
+        except Exception:
+            continue
+        if gd.get("workload") == workload_name and f"F_{grad}" in gd:
+            return path, gd
+    return None
+
+
+def err_vs_short_golden(A, W, w, args, dev):
+    """Where no golden covers the timed pulse (the L = 24 chain: its oracle needs ~1.4 h of CPU for
+    12 slices), evaluate the golden's shorter pulse once, untimed, with the same engine options (the
+    checkpoint interval capped at the pulse's N - 1), and return the relative errors against it."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+    found = short_pulse_golden(args.workload, args.grad)
+    if found is None or args.grad not in ("centered", "zeroth"):
+        return None
+    path, gd = found
+    n = int(gd["N"])
+    ws = dataclasses.replace(w, N=n)
+    u, psi0, f = W.instance(ws)
+    ck = min(w.ckpt, max(n - 1, 0)) if w.ckpt > 0 else w.ckpt
+    eng = A.KGrape(A.ChainSpec(w.L, w.Jxy, w.Jz), A.Options(n, w.dt, w.m, prec=args.prec, ckpt_every=ck,
+                                                             grad=args.grad, reorth=args.reorth), device=dev)
+    fid, grad = eng.evaluate(torch.tensor(u, device=dev), torch.tensor(psi0, device=dev),
+                             torch.tensor(f, device=dev))
+    eng.sync()
+    F = float(fid.item())
+    g = grad[:n].cpu().numpy()
+    eng.close()
+    ref = np.asarray(gd[f"grad_{args.grad}"])
+    return {"F": abs(F - gd[f"F_{args.grad}"]) / abs(gd[f"F_{args.grad}"]),
+            "grad": float(np.linalg.norm(g - ref) / np.linalg.norm(ref)),
+            "golden": os.path.relpath(path, ROOT), "N": n, "ckpt_every": ck,
+            "note": "a shorter pulse of the same workload, evaluated untimed with the timed options"}
+
+
 def ncu_traffic(kernel_key: str):
     """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -403,6 +448,8 @@ def run_ours(args):
         if args.grad != "centered" and cpu.get("sample"):
             cpu["sample"] += "; the oracle's centred gradient, not the timed gradient mode"
     err = err_vs_oracle(args, w, fid, grad)
+    if err is None and rank == 0 and args.N == 0:  # the workload's own pulse length only
+        err = err_vs_short_golden(A, W, w, args, dev)
     emit(rank, world, args, w, value, ms_per_step, roofline, cpu, e2e, clocks, fp64, rep, fid, wall, err)
     if world > 1:
         dist.destroy_process_group()
