@@ -301,7 +301,7 @@ kg_status kg_evaluate_static(const kg_chain* chain, const kg_options* opts, cons
  * the smaller member of an orbit is the same whichever end the number starts from).  For states in
  * the subspace, F and the gradient equal those of the full 2^L chain.  Vectors (psi0, target) are
  * complex128 in this basis; the Krylov sweeps, gradient modes and precisions are those of
- * kg_evaluate.  Each problem of a batch (one control pulse each) runs on one CTA, with the whole
+ * kg_evaluate, plus KG_PREC_FF (float-float vectors, subspaces only).  Each problem of a batch (one control pulse each) runs on one CTA, with the whole
  * state in shared memory; CTAs take problems b, b + grid, b + 2 grid, ...  No device-side wait. */
 typedef struct kg_sector {
   int32_t L;               /* number of spins, 2 <= L <= 30 */
@@ -309,7 +309,8 @@ typedef struct kg_sector {
   int32_t parity;          /* +1 even, -1 odd, 0 the whole K-excitation sector */
   int32_t block_threads;   /* threads per CTA (one pulse per CTA): 0 = chosen from D, or 128, 256,
                               512; with rows per thread of 4 (128), 10 (256, complex64) or 8 (256,
-                              complex128; 512) the block must cover D, else KG_ERR_INVALID_ARG.  The
+                              complex128 and float-float; 512) the block must cover D, else
+                              KG_ERR_INVALID_ARG.  The
                               block shape changes only the speed (kg_sector_* results are the same to
                               rounding); tune.py times the shapes */
   uint64_t hc_site_mask;   /* sites of the Sz terms of Hc (bits < L); mirror-symmetric if parity != 0 */
@@ -336,7 +337,8 @@ kg_status kg_sector_states(const kg_sector* sector, uint64_t* states, int32_t D)
 kg_status kg_sector_apply_h0(const kg_sector* sector, const double* v, double* w, int32_t D);
 
 /* Workspace bytes for B pulses with options opts (N, m <= 32, prec, grad NONE / CENTERED / ZEROTH /
- * EXACT / TAYLOR1 / TAYLOR2 (EXACT keeps 2N interior states per CTA),
+ * EXACT / TAYLOR1 / TAYLOR2 (EXACT keeps 2N interior states per CTA; KG_PREC_FF takes NONE, CENTERED
+ * and ZEROTH only, else KG_ERR_UNSUPPORTED; its vectors take 16 bytes per amplitude),
  * dt, breakdown_tol, ctas = most CTAs to use (0 = every one that fits); ckpt_every and tile_bits
  * must be 0; flags: KG_FLAG_PHASE_TIMING only, recording CTA 0's cycles in kg_report.phase_cycles as
  * [0] Lanczos gathers and updates, [1] block reductions, [4] tridiagonal T and small exponential,
