@@ -57,9 +57,10 @@ typedef enum kg_precision {
                               norms, the m x m exponential and <f|psi_N> in FP64 */
   KG_PREC_FF = 2           /* float-float vectors: each real part and imaginary part is the
                               unevaluated sum hi + lo of two FP32 numbers (about 44 significant
-                              bits), H*v, the Lanczos updates and the recombination in FP32 with
-                              error-free transformations (TwoSum, FMA TwoProduct); recurrences,
-                              norms, the m x m exponential and the overlaps in FP64.  16 bytes per
+                              bits), H*v, the Lanczos updates, the recombination and the Lanczos
+                              sums and scalars in FP32 with error-free transformations (TwoSum,
+                              FMA TwoProduct); the tridiagonal, the m x m exponential, the per-slice
+                              norms and the overlaps in FP64.  16 bytes per
                               amplitude, like complex128.  Subspace engines (kg_sector_*) only,
                               with KG_GRAD_NONE, _CENTERED or _ZEROTH: it carries the paper's
                               subspace task (Sec. 3.2: 2 x 4D slices of dt = 0.5) to 1e-5 of the

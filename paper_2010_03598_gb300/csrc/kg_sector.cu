@@ -72,12 +72,36 @@ __device__ __forceinline__ FFR operator*(FFR a, FFR b) {
   return FFR(p.hi, p.lo);
 }
 __device__ __forceinline__ FFR fma(FFR a, FFR b, FFR c) { return a * b + c; }
-// Scalar operations (once per Lanczos step, not per amplitude) go through FP64.
-__device__ __forceinline__ FFR operator/(FFR a, FFR b) { return FFR((double)a / (double)b); }
-__device__ __forceinline__ bool operator<=(FFR a, FFR b) { return (double)a <= (double)b; }
-__device__ __forceinline__ FFR fmax(FFR a, FFR b) { return ((double)a >= (double)b) ? a : b; }
+// Square root and reciprocal: the FP32 estimate refined by one Newton step carried out in
+// float-float (the residual a - s^2, or 1 - b y, formed exactly with an FMA), about 44 bits.
+__device__ __forceinline__ FF ff_sqrt(FF a) {
+  if (!(a.hi > 0.f)) return FF{0.f, 0.f};
+  const float s = sqrtf(a.hi);
+  const float p = __fmul_rn(s, s);
+  const float e = __fmaf_rn(s, s, -p);                                      // s^2 = p + e exactly
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);       // a - s^2
+  return ff_two_sum(s, __fdiv_rn(r, __fmul_rn(2.f, s)));
+}
+__device__ __forceinline__ FF ff_rcp(FF b) {
+  const float y = __frcp_rn(b.hi);
+  const float p = __fmul_rn(b.hi, y);
+  const float pe = __fmaf_rn(b.hi, y, -p);                                  // b.hi y = p + pe exactly
+  const float r = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(b.lo, y));  // 1 - b y
+  return ff_two_sum(y, __fmul_rn(y, r));
+}
+// Scalar operations, once per Lanczos step: comparisons on (hi, lo) in order.
+__device__ __forceinline__ bool ffr_less(FFR a, FFR b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ FFR operator/(FFR a, FFR b) {
+  const FF q = ff_rcp(FF{b.hi, b.lo});
+  return a * FFR(q.hi, q.lo);
+}
+__device__ __forceinline__ bool operator<=(FFR a, FFR b) { return !ffr_less(b, a); }
+__device__ __forceinline__ FFR fmax(FFR a, FFR b) { return ffr_less(a, b) ? b : a; }
 __device__ __forceinline__ FFR fabs(FFR a) { return (a.hi < 0.f) ? -a : a; }
-__device__ __forceinline__ FFR sqrt(FFR a) { return FFR(::sqrt((double)a)); }
+__device__ __forceinline__ FFR sqrt(FFR a) {
+  const FF s = ff_sqrt(FF{a.hi, a.lo});
+  return FFR(s.hi, s.lo);
+}
 // the float and double functions stay visible beside these overloads inside namespace kg
 using ::fma;
 using ::fmax;
@@ -195,6 +219,30 @@ __device__ __forceinline__ void sec_reduce(SecSmem& sm, int& par, const double (
   sec_sync();
 #pragma unroll
   for (int v = 0; v < NV; ++v) out[v] = sm.tot_d[par][v];
+  par ^= 1;
+}
+
+// Float-float partial sums (KG_PREC_FF): the same two stages, warp sums by ff_add (the warp partials
+// are kept in the complex128 path's slots, two floats in each).
+template <int NT, int NV>
+__device__ __forceinline__ void sec_reduce(SecSmem& sm, int& par, const FF (&vals)[NV], FF (&out)[NV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* red = reinterpret_cast<float2*>(sm.red_d[par]);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const FF x = ff_warp_sum(vals[v]);
+    if (lane == 0) red[warp * 4 + v] = make_float2(x.hi, x.lo);
+  }
+  sec_sync();
+  if (warp < NV) {
+    FF s{0.f, 0.f};
+    if (lane < NT / 32) s = FF{red[lane * 4 + warp].x, red[lane * 4 + warp].y};
+    s = ff_warp_sum(s);
+    if (lane == 0) sm.tot_f[par][warp] = make_float2(s.hi, s.lo);
+  }
+  sec_sync();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = FF{sm.tot_f[par][v].x, sm.tot_f[par][v].y};
   par ^= 1;
 }
 
@@ -486,6 +534,46 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
       }
       alpha = st.alpha;
       b2 = st.b2;
+    } else if constexpr (FFM) {
+      // float-float sums and scalars: alpha_k and b_{k+1}^2 = ||w||^2 + alpha^2 (||v||^2 - 2) in
+      // float-float, as the complex64 path forms them, but kept at float-float for the vectors
+      const FF vals[3] = {FF{pa.hi, pa.lo}, FF{pn.hi, pn.lo}, FF{pq.hi, pq.lo}};
+      FF o[3];
+      sec_mark(p, sm, 0);
+      sec_reduce<NT, 3>(sm, par, vals, o);
+      sec_mark(p, sm, 1);
+      if (!isfinite(o[0].hi) || !isfinite(o[1].hi)) {
+        if (tid == 0) {
+          sec_flag(p, KG_ERR_NONFINITE);
+          sec_record(sm, k, 1);
+        }
+        return false;
+      }
+      FF b2ff = ff_add(o[1], ff_mul(ff_mul(o[0], o[0]), ff_add(o[2], FF{-2.f, 0.f})));
+      if (tid == 0) {
+        sm.ff_a[k] = make_float2(o[0].hi, o[0].lo);
+        sm.ff_n[k] = make_float2(o[1].hi, o[1].lo);
+        sm.ff_q[k] = make_float2(o[2].hi, o[2].lo);
+      }
+      if (!last && b2ff.hi < 1e-3f * o[1].hi) {  // near an invariant subspace: ||w - alpha v||^2 explicitly
+        const R ra = R(o[0].hi, o[0].lo);
+        R e = 0;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const V d = vaxpy<V>(-ra, vv[i], w[i]);
+          e = fma(d.x, d.x, fma(d.y, d.y, e));
+        }
+        const FF e1[1] = {FF{e.hi, e.lo}};
+        FF o1[1];
+        sec_reduce<NT, 1>(sm, par, e1, o1);
+        if (tid == 0) {
+          sm.ff_e[k] = make_float2(o1[0].hi, o1[0].lo);
+          sm.ff_e_set |= 1u << k;
+        }
+        b2ff = o1[0];
+      }
+      alpha = R(o[0].hi, o[0].lo);
+      b2 = R(b2ff.hi, b2ff.lo);
     } else {
       const double vals[3] = {(double)pa, (double)pn, (double)pq};
       double o[3];
@@ -556,7 +644,7 @@ __device__ __forceinline__ bool sec_slice(const SectorParams& p, SecSmem& sm, in
   if (tid < 32) {
     __syncwarp();  // thread 0's stores of the step sums are visible to the warp
     const int k = tid;
-    if constexpr (F32) {
+    if constexpr (F32 || FFM) {
       if (k < meff) {
         const double al = ff_to_double(FF{sm.ff_a[k].x, sm.ff_a[k].y});
         double b2;
