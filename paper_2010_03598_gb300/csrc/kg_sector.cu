@@ -1027,14 +1027,17 @@ static SecKernel sec_choice() {
 // thread (10 for complex64 up to 2560, which keeps two CTAs on an SM); or, with nt = 128, 256 or
 // 512 threads, that block with the fewest rows per thread that covers D (nt.threads == 0: none).
 static SecKernel sec_pick(int prec, int D, int nt = 0) {
-  if (prec == KG_PREC_FF) {  // the complex128 path's shapes (16-byte amplitudes)
+  if (prec == KG_PREC_FF) {  // the complex128 path's shapes (16-byte amplitudes); 512 x 5 up to
+                             // D = 2560 holds its arrays in registers (512 x 8 spills)
     if (nt == 128) return (D <= 512) ? sec_choice<FFC, 128, 4>() : SecKernel{nullptr, 0};
     if (nt == 256) return (D <= 1024) ? sec_choice<FFC, 256, 4>()
                                       : (D <= 2048) ? sec_choice<FFC, 256, 8>() : SecKernel{nullptr, 0};
-    if (nt == 512) return (D <= 4096) ? sec_choice<FFC, 512, 8>() : SecKernel{nullptr, 0};
+    if (nt == 512)
+      return (D <= 2560) ? sec_choice<FFC, 512, 5>() : (D <= 4096) ? sec_choice<FFC, 512, 8>() : SecKernel{nullptr, 0};
     if (D <= 512) return sec_choice<FFC, 128, 4>();
     if (D <= 1024) return sec_choice<FFC, 256, 4>();
     if (D <= 2048) return sec_choice<FFC, 256, 8>();
+    if (D <= 2560) return sec_choice<FFC, 512, 5>();
     return sec_choice<FFC, 512, 8>();
   }
   if (prec == KG_PREC_C128) {
