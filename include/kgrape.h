@@ -310,7 +310,7 @@ typedef struct kg_sector {
   int32_t parity;          /* +1 even, -1 odd, 0 the whole K-excitation sector */
   int32_t block_threads;   /* threads per CTA (one pulse per CTA): 0 = chosen from D, or 128, 256,
                               512; with rows per thread of 4 (128), 10 (256, complex64) or 8 (256,
-                              complex128 and float-float; 512, where float-float takes 5 rows up to
+                              complex128 and float-float; 512, where these two take 5 rows up to
                               D = 2560) the block must cover D, else KG_ERR_INVALID_ARG.  The
                               block shape changes only the speed (kg_sector_* results are the same to
                               rounding); tune.py times the shapes */

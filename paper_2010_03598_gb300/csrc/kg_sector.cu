@@ -1040,14 +1040,17 @@ static SecKernel sec_pick(int prec, int D, int nt = 0) {
     if (D <= 2560) return sec_choice<FFC, 512, 5>();
     return sec_choice<FFC, 512, 8>();
   }
-  if (prec == KG_PREC_C128) {
+  if (prec == KG_PREC_C128) {  // 512 x 5 up to D = 2560 spills less than 512 x 8
     if (nt == 128) return (D <= 512) ? sec_choice<double2, 128, 4>() : SecKernel{nullptr, 0};
     if (nt == 256) return (D <= 1024) ? sec_choice<double2, 256, 4>()
                                       : (D <= 2048) ? sec_choice<double2, 256, 8>() : SecKernel{nullptr, 0};
-    if (nt == 512) return (D <= 4096) ? sec_choice<double2, 512, 8>() : SecKernel{nullptr, 0};
+    if (nt == 512)
+      return (D <= 2560) ? sec_choice<double2, 512, 5>()
+                         : (D <= 4096) ? sec_choice<double2, 512, 8>() : SecKernel{nullptr, 0};
     if (D <= 512) return sec_choice<double2, 128, 4>();
     if (D <= 1024) return sec_choice<double2, 256, 4>();
     if (D <= 2048) return sec_choice<double2, 256, 8>();
+    if (D <= 2560) return sec_choice<double2, 512, 5>();
     return sec_choice<double2, 512, 8>();
   }
   if (nt == 128) return (D <= 512) ? sec_choice<float2, 128, 4>() : SecKernel{nullptr, 0};
