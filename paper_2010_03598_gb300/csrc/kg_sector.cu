@@ -981,10 +981,13 @@ __device__ __forceinline__ void sec_eval(const SectorParams& p, int b, SecSmem& 
 // CTAs (pulses) per SM the register allocation is sized for.  A pulse is a chain of latencies
 // (block barriers, FP64 on warp 0), so pulses sharing an SM hide each other's: complex64 blocks of
 // 128 threads are held to 64 registers a thread, eight pulses per SM (a few spills; measured 1.9x the
-// pulses/s of three per SM at D = 511); other blocks of up to 256 threads to 128 registers, two per SM.
+// pulses/s of three per SM at D = 511); float-float blocks of 128 threads to 128 registers, four per
+// SM (no spills; 732 against 626 pulses/s at three per SM, D = 511); other blocks of up to 256
+// threads to 128 registers, two per SM.
 template <class V, int NT>
 constexpr int sec_min_blocks() {
-  return (NT == 128 && sizeof(V) == sizeof(float2)) ? 8 : (NT <= 256) ? 2 : 1;
+  return (NT == 128 && sizeof(V) == sizeof(float2)) ? 8 : (NT == 128 && std::is_same<V, FFC>::value) ? 4
+                                                    : (NT <= 256) ? 2 : 1;
 }
 
 template <class V, int NT, int RPT>
