@@ -174,3 +174,25 @@ def test_closed_form_limit_keeps_odd_subspaces_near_the_limit():
     for par in (1, -1):
         assert _abi.lib().kg_sector_dim(ctypes.byref(A.SectorSpec(16, 8, par).to_c()),
                                         ctypes.byref(D)) == _abi.KG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128", "ff"])
+@pytest.mark.parametrize("L,K", [(14, 4), (20, 4)])
+def test_block_shapes_the_library_accepts_are_the_tuners_candidates(prec, L, K):
+    # kg_sector_workspace_bytes answers KG_ERR_INVALID_ARG for a block that cannot cover D; the
+    # autotuner must offer exactly the shapes it accepts (float-float takes the complex128 shapes)
+    import dataclasses
+
+    from paper_2010_03598_gb300 import tune
+    D = A.sector_dim(A.SectorSpec(L, K, 1))
+    ok = set()
+    for nt in (0, 128, 256, 512):
+        spec = dataclasses.replace(A.SectorSpec(L, K, 1), block_threads=nt)
+        o = A.Options(N=16, dt=0.5, m=10, prec=prec)
+        n = ctypes.c_size_t(0)
+        st = _abi.lib().kg_sector_workspace_bytes(ctypes.byref(spec.to_c()), ctypes.byref(o.to_c()), 4,
+                                                  ctypes.byref(n))
+        assert st in (_abi.KG_OK, _abi.KG_ERR_INVALID_ARG)
+        if st == _abi.KG_OK:
+            ok.add(nt)
+    assert ok == {c["block_threads"] for c in tune.sector_candidates(D, prec, 152)}

@@ -70,6 +70,9 @@ def test_candidate_lists():
     assert {c["block_threads"] for c in sec} == {0, 256, 512}  # 128 x 4 rows cannot cover D = 2445
     assert {c["block_threads"] for c in tune.sector_candidates(511, "c64", 152)} == {0, 128, 256, 512}
     assert {c["block_threads"] for c in tune.sector_candidates(2445, "c128", 152)} == {0, 512}
+    # float-float vectors take the complex128 path's shapes (16-byte amplitudes)
+    assert {c["block_threads"] for c in tune.sector_candidates(2445, "ff", 152)} == {0, 512}
+    assert {c["block_threads"] for c in tune.sector_candidates(511, "ff", 152)} == {0, 128, 256, 512}
     bc = tune.batch_candidates(152)
     assert len(bc) == 4 and len(tune.batch_candidates(150)) == 6  # 152 SMs are already a multiple of 8
     assert all(c["ctas"] <= 152 for c in tune.single_candidates(20, "c64", 152))
